@@ -1,0 +1,257 @@
+"""Python front end of the plain FP64 CPU oracle (``treeray_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke``
+and by the CPU-baseline leg of ``bench.py``; the CUDA library never calls it.
+The C source is the oracle; this module compiles it with gcc and marshals
+numpy arrays through ctypes.  Nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "treeray_oracle.c")
+_HDR = os.path.join(_HERE, "treeray_oracle.h")
+_LIB = os.path.join(_HERE, "libtreeray_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TQH, TQ, TB, TM = 16, 33, 40, 8
+NKEYS = 6 * TQ * TQ * TB
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library next to its source."""
+    stale = (not os.path.exists(_LIB)
+             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("dx_cm", C.c_double), ("nside", C.c_int32),
+                ("eta_r", C.c_int32), ("theta_lim", C.c_double), ("theta_if", C.c_double),
+                ("theta_src", C.c_double), ("lray_cells", C.c_double),
+                ("alpha_B", C.c_double), ("hnu", C.c_double), ("zeta_g", C.c_int32)]
+
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_U8 = C.POINTER(C.c_uint8)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_ang2pix.restype = C.c_int64
+            L.orc_ang2pix.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double]
+            L.orc_pix2vec.argtypes = [C.c_int32, C.c_int64, _D]
+            L.orc_num_points.restype = C.c_int32
+            L.orc_num_points.argtypes = [C.c_int32, C.c_double]
+            L.orc_radius.restype = C.c_double
+            L.orc_radius.argtypes = [C.c_int32, C.c_int32]
+            L.orc_wp.restype = C.c_double
+            L.orc_wp.argtypes = [C.c_double]
+            L.orc_wf3_split.argtypes = [C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_wp_weights.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_table_key.restype = C.c_int32
+            L.orc_table_key.argtypes = [C.c_int64] * 4
+            L.orc_table_entry.restype = C.c_int32
+            L.orc_table_entry.argtypes = [C.c_int32, C.c_int32, _I32, _I32, C.c_int32]
+            L.orc_sweep_ray.restype = C.c_double
+            L.orc_sweep_ray.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _D, _D, _D,
+                                        C.c_double, _D, _D]
+            L.orc_tree_build.restype = C.c_void_p
+            L.orc_tree_build.argtypes = [C.c_int32, C.c_double, C.c_double, _D, _D, _D,
+                                         C.c_int32, _D, _D, _D]
+            L.orc_tree_free.argtypes = [C.c_void_p]
+            L.orc_tree_levels.restype = C.c_int32
+            L.orc_tree_levels.argtypes = [C.c_void_p]
+            L.orc_tree_node.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64, _D]
+            L.orc_cell_quantities.argtypes = [C.c_void_p, _D, _D, _D]
+            L.orc_walk_target.restype = C.c_int64
+            L.orc_walk_target.argtypes = [C.c_void_p, C.POINTER(Params), C.c_int64, _D, _D, _D,
+                                          _I64, C.c_int64, _I64]
+            L.orc_solve_pass.restype = C.c_int32
+            L.orc_solve_pass.argtypes = [C.c_void_p, C.POINTER(Params), _I64, C.c_int64, _D, _D, _U8]
+            L.orc_solve.restype = C.c_int32
+            L.orc_solve.argtypes = [C.POINTER(Params), _D, _D, _D, C.c_int32, _D, _D, _D,
+                                    C.c_int32, C.c_double, C.c_int32, _D, _D, _U8, _I32, _D]
+            L.orc_delta.restype = C.c_double
+            L.orc_delta.argtypes = [C.c_int64, _D, _D, C.c_int32]
+            _lib = L
+    return _lib
+
+
+def _p(a, ctype=_D):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctype)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def ang2pix(nside: int, v) -> int:
+    return int(lib().orc_ang2pix(nside, float(v[0]), float(v[1]), float(v[2])))
+
+
+def pix2vec(nside: int, pix: int) -> np.ndarray:
+    out = np.zeros(3)
+    lib().orc_pix2vec(nside, pix, _p(out))
+    return out
+
+
+def num_points(eta_r: int, lray_cells: float) -> int:
+    return int(lib().orc_num_points(eta_r, lray_cells))
+
+
+def radius(i: int, eta_r: int) -> float:
+    return float(lib().orc_radius(i, eta_r))
+
+
+def wp(x: float) -> float:
+    return float(lib().orc_wp(x))
+
+
+def wp_weights(d: float, h: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_wp_weights(d, h, nr, eta_r, _p(out))
+    return out
+
+
+def wf3_split(d: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_wf3_split(d, nr, eta_r, _p(out))
+    return out
+
+
+def table_key(o, s: int) -> int:
+    return int(lib().orc_table_key(int(o[0]), int(o[1]), int(o[2]), int(s)))
+
+
+def table_entry(nside: int, key: int, cap: int = 4096):
+    pix = np.zeros(cap, dtype=np.int32)
+    cnt = np.zeros(cap, dtype=np.int32)
+    n = lib().orc_table_entry(nside, key, _p(pix, _I32), _p(cnt, _I32), cap)
+    return pix[:n].copy(), cnt[:n].copy()
+
+
+def sweep_ray(alpha_vol, eps, e_vol=None, *, eta_r=2, nside=2, zeta_g=True, kd=0.0):
+    a = _f64(alpha_vol)
+    e = _f64(eps)
+    ev = _f64(e_vol)
+    nr = a.shape[0]
+    phi0 = np.zeros(nr)
+    loss = np.zeros(nr)
+    F0 = lib().orc_sweep_ray(nr, eta_r, nside, int(zeta_g), _p(a), _p(e), _p(ev), kd,
+                             _p(phi0), _p(loss))
+    return float(F0), phi0, loss
+
+
+def params_for(w, *, zeta_g: bool = True, lray_cells: float = 0.0, **over) -> Params:
+    """Oracle parameters for a :class:`workloads.Workload` (overrides by keyword)."""
+    d = dict(N=w.N, dx_cm=w.dx, nside=w.nside, eta_r=w.eta_r, theta_lim=w.theta_lim,
+             theta_if=w.theta_if, theta_src=w.theta_src, lray_cells=lray_cells,
+             alpha_B=w.alpha_B, hnu=w.hnu, zeta_g=int(zeta_g))
+    d.update(over)
+    return Params(**d)
+
+
+class Tree:
+    """Oracle octree over a uniform N^3 grid (Sec. 2.1)."""
+
+    def __init__(self, w, e_prev=None, box_lo=(0.0, 0.0, 0.0)):
+        self.N = w.N
+        self._keep = [_f64(w.n_H).ravel(), _f64(w.ndot_cell).ravel() if w.ndot_cell is not None else None,
+                      _f64(w.src_xyz).reshape(-1), _f64(w.src_Q), _f64(e_prev).ravel() if e_prev is not None else None,
+                      np.asarray(box_lo, dtype=np.float64)]
+        nH, nd, xyz, q, ep, lo = self._keep
+        self.h = lib().orc_tree_build(w.N, w.dx, w.alpha_B, _p(lo), _p(nH), _p(nd),
+                                      int(q.shape[0]), _p(xyz), _p(q), _p(ep))
+        self.use_e = e_prev is not None
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_tree_free(self.h)
+            self.h = None
+
+    @property
+    def levels(self) -> int:
+        return int(lib().orc_tree_levels(self.h))
+
+    def node(self, level, ix, iy, iz) -> np.ndarray:
+        out = np.zeros(8)
+        lib().orc_tree_node(self.h, level, ix, iy, iz, _p(out))
+        return out
+
+    def cell_quantities(self):
+        nc = self.N ** 3
+        nd, a, e = np.zeros(nc), np.zeros(nc), np.zeros(nc)
+        lib().orc_cell_quantities(self.h, _p(nd), _p(a), _p(e))
+        return nd, a, e
+
+    def walk(self, p: Params, target: int, cap: int = 1 << 16):
+        nr = num_points(p.eta_r, p.lray_cells if p.lray_cells > 0 else p.N * math.sqrt(3.0))
+        npix = 12 * p.nside * p.nside
+        ba, be = np.zeros(npix * nr), np.zeros(npix * nr)
+        bee = np.zeros(npix * nr) if self.use_e else None
+        acc = np.zeros(cap, dtype=np.int64)
+        nacc = np.zeros(1, dtype=np.int64)
+        visited = lib().orc_walk_target(self.h, C.byref(p), int(target), _p(ba), _p(be), _p(bee),
+                                        _p(acc, _I64), cap, _p(nacc, _I64))
+        n = int(nacc[0])
+        return dict(visited=int(visited), accepted=acc[:min(n, cap)].copy(), n_accepted=n,
+                    alpha=ba.reshape(npix, nr), eps=be.reshape(npix, nr),
+                    e=None if bee is None else bee.reshape(npix, nr))
+
+    def solve_pass(self, p: Params, targets=None):
+        if targets is None:
+            n = self.N ** 3
+            tp = None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            n = targets.shape[0]
+            tp = _p(targets, _I64)
+        F, e, ion = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.uint8)
+        lib().orc_solve_pass(self.h, C.byref(p), tp, n, _p(F), _p(e), _p(ion, _U8))
+        return F, e, ion
+
+
+def solve(w, p: Params, *, e_init=None, max_iter: int = 1, eps_lim: float = 1e-2,
+          delta_mode: int = 0, box_lo=(0.0, 0.0, 0.0)):
+    """Full oracle solve with the outer iteration (Sec. 2.6)."""
+    nc = w.N ** 3
+    nH = _f64(w.n_H).ravel()
+    nd = _f64(w.ndot_cell).ravel() if w.ndot_cell is not None else None
+    xyz = _f64(w.src_xyz).reshape(-1)
+    q = _f64(w.src_Q)
+    ei = _f64(e_init).ravel() if e_init is not None else None
+    lo = np.asarray(box_lo, dtype=np.float64)
+    F, e, ion = np.zeros(nc), np.zeros(nc), np.zeros(nc, dtype=np.uint8)
+    iters = np.zeros(1, dtype=np.int32)
+    delta = np.zeros(1)
+    lib().orc_solve(C.byref(p), _p(lo), _p(nH), _p(nd), int(q.shape[0]), _p(xyz), _p(q), _p(ei),
+                    max_iter, eps_lim, delta_mode, _p(F), _p(e), _p(ion, _U8),
+                    _p(iters, _I32), _p(delta))
+    return F, e, ion, int(iters[0]), float(delta[0])
+
+
+def delta(e_new, e_old, mode: int = 0) -> float:
+    a, b = _f64(e_new).ravel(), _f64(e_old).ravel()
+    return float(lib().orc_delta(a.shape[0], _p(a), _p(b), mode))
