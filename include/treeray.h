@@ -1,0 +1,177 @@
+/* treeray.h - C ABI of the GB300 (sm_103a) TreeRay/OnTheSpot hot path.
+ *
+ * The method is TreeRay/OnTheSpot (Wuensch et al., arXiv 2105.09644):
+ * for every target cell the octree is walked with the opening criteria of
+ * Sec. 2.4, accepted nodes are mapped onto N_PIX HEALPix rays x N_R radial
+ * evaluation points (Sec. 2.2-2.3, App. A), each ray is swept from far to
+ * near with the On-the-Spot recombination loss (Sec. 2.5, Eq. 12-17) and the
+ * rays are summed into the cell's EUV photon flux and energy density
+ * (Eq. 18).  Sec. 2.6 (Eq. 19-21) iterates this until the energy density
+ * converges.
+ *
+ * Conventions shared by every call
+ *  - All array arguments are DEVICE pointers on the current CUDA device,
+ *    owned by the caller, unless a comment says otherwise.  Cell arrays hold
+ *    N^3 values of a uniform cubic grid in C order [iz][iy][ix] (x fastest).
+ *  - Units are CGS: cm, cm^-3, photons s^-1, erg.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default).
+ *    Calls that report device-side status synchronise that stream before
+ *    returning, as noted.
+ *  - No call aborts or throws.  A call returns TR_OK or an error code and
+ *    leaves a thread-local message for tr_last_error().
+ *  - Opaque handles (tr_tree, tr_rays) are owned by the library and released
+ *    with their *_free function.
+ */
+#ifndef TREERAY_H
+#define TREERAY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tr_stream;   /* same type as cudaStream_t */
+
+typedef enum {
+    TR_OK = 0,
+    TR_EINVAL = 1,          /* bad argument (null pointer, size, parameter range) */
+    TR_ENOMEM = 2,          /* device allocation failed */
+    TR_ECUDA = 3,           /* a CUDA call failed (message has the CUDA error) */
+    TR_ETIMEOUT = 4,        /* a bounded device-side wait ran out */
+    TR_EUNSUPPORTED = 5,    /* valid request outside what this build implements */
+    TR_EOVERFLOW = 6        /* a per-target walk stack overflowed; raise theta or report */
+} tr_status;
+
+typedef enum {
+    TR_FP64 = 0,            /* node moments, deposits and sweep all in FP64 */
+    TR_FP32_SWEEP64 = 1     /* FP32 node moments and ray deposits with compensated
+                               (Kahan-Neumaier) sums; FP64 sweep and classification */
+} tr_precision;
+
+/* Solver parameters (Sec. 2.2-2.6).  tr_params_default() fills the paper's
+ * defaults: theta_lim 0.5, theta_if = theta_src = INFINITY, N_side 2,
+ * eta_R 2, L_ray = domain diagonal, alpha_B 2.7e-13, h nu = 13.6 eV,
+ * eps_lim 1e-2, delta per cell, one pass, FP64, zeta_g on. */
+typedef struct {
+    double theta_lim;       /* BH opening angle: accept when h/d < theta_lim (Sec. 2.4) */
+    double theta_if;        /* IF MAC angle, INFINITY disables (Sec. 2.4) */
+    double theta_src;       /* Src MAC angle, INFINITY disables (Sec. 2.4) */
+    int32_t nside;          /* HEALPix N_side in {1, 2, 4, 8}; N_PIX = 12 N_side^2 (Sec. 2.2) */
+    int32_t eta_r;          /* radial resolution eta_R in {1, 2, 4, 8} (Eq. 4) */
+    double L_ray_cm;        /* maximum ray length; <= 0 selects the domain diagonal (Eq. 5) */
+    double alpha_B;         /* case-B recombination coefficient, cm^3 s^-1 */
+    double hnu;             /* mean EUV photon energy, erg */
+    double eps_lim;         /* iteration stops when delta < eps_lim (Sec. 2.6) */
+    int32_t delta_mode;     /* 0: delta_cell (Eq. 21), 1: delta_tot (Eq. 20) */
+    int32_t max_iter;       /* >= 1 passes of build + walk + sweep */
+    int32_t precision;      /* tr_precision */
+    int32_t zeta_g;         /* 1: apply the geometric factor zeta_g (Eq. 16) */
+} tr_params;
+
+/* Uniform cubic grid.  N is a power of two with 8 <= N <= 512.
+ * n_H: hydrogen number density (cm^-3), required, finite and >= 0.
+ * ndot: extra per-cell EUV emission (photons s^-1), may be NULL.
+ * e_prev: per-cell EUV energy density (erg cm^-3) from a previous pass, may
+ *         be NULL; it enters the IF MAC (ionised mass, Sec. 2.4) and zeta_d
+ *         (Eq. 17), and seeds the iteration of tr_solve (Sec. 2.6). */
+typedef struct {
+    int32_t N;
+    double box_lo[3];       /* low corner of the box, cm */
+    double dx;              /* cell edge, cm */
+    const double* n_H;
+    const double* ndot;
+    const double* e_prev;
+} tr_grid;
+
+/* Point sources (Sec. 2.7), mapped to the cell containing them. */
+typedef struct {
+    int32_t n;              /* number of sources, >= 0 */
+    const double* xyz;      /* device, n x 3 positions, cm */
+    const double* Q;        /* device, n EUV photon rates, s^-1 */
+} tr_sources;
+
+typedef struct tr_tree tr_tree;
+typedef struct tr_rays tr_rays;
+
+/* Fill *p with the defaults listed above. */
+void tr_params_default(tr_params* p);
+
+/* Build the octree (Sec. 2.1, Eq. 1-3): sources are mapped to cells
+ * (Sec. 2.7), emission and recombination are netted per cell, and node
+ * moments (mass, centre of mass, alpha_n, eps_n, e_n, ionised mass) are
+ * reduced bottom-up in Morton order.  *out may hold a tree from an earlier
+ * call: it is rebuilt in place when its grid size and precision match,
+ * otherwise it is freed and replaced.  The node->ray table for N_side is
+ * built on the device on first use and cached for the process.
+ * Errors: TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_EUNSUPPORTED.  Asynchronous. */
+tr_status tr_build_tree(const tr_grid* g, const tr_sources* s, const tr_params* p,
+                        tr_tree** out, tr_stream stream);
+
+/* Walk the tree for n_targets target cells (C-order cell indices, device
+ * int64 array; NULL with n_targets = N^3 means every cell) and map the
+ * accepted nodes onto each target's rays (Sec. 2.3-2.4).  The result keeps,
+ * per target, the ray bins alpha/eps/e ([N_PIX][N_R] each) and the list of
+ * accepted node ids (level-order Morton numbering: (8^l - 1)/7 + Morton
+ * index within level l).  Meant for parity checks and the unfused path;
+ * device memory grows with n_targets x N_PIX x N_R.  Synchronises `stream`.
+ * Errors: TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_EOVERFLOW. */
+tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_targets,
+                      tr_rays** out, tr_stream stream);
+
+/* Sweep every ray of a tr_rays far to near (Sec. 2.5, Eq. 12-17) in FP64 and
+ * sum the directions (Eq. 18).  Outputs (device, n_targets each, may be NULL):
+ * F_out photon flux (photons s^-1 cm^-2), e_out energy density (erg cm^-3),
+ * ion_out 1 where F > 0.  Asynchronous. */
+tr_status tr_ray_sweep(const tr_rays* r, double* F_out, double* e_out, uint8_t* ion_out,
+                       tr_stream stream);
+
+/* The fused fast path: build + walk + map + sweep for every cell, repeated
+ * (Sec. 2.6) until delta < eps_lim or max_iter passes.  Outputs are N^3
+ * device arrays (NULL allowed): F_out, e_out, ion_out as in tr_ray_sweep.
+ * iters_out and delta_out are HOST pointers (may be NULL).  Device memory
+ * is cached per device between calls and grows on demand.  Synchronises
+ * `stream`.  Errors: TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_EOVERFLOW. */
+tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p,
+                   double* F_out, double* e_out, uint8_t* ion_out,
+                   int32_t* iters_out, double* delta_out, tr_stream stream);
+
+/* ---- inspection (parity tests) -------------------------------------- */
+
+/* Sizes of a tree: node count, levels (log2 N + 1), N_R, N_PIX. Host outputs. */
+tr_status tr_tree_info(const tr_tree* t, int64_t* n_nodes, int32_t* levels,
+                       int32_t* nr, int32_t* npix);
+
+/* Node records as FP64 in level-order Morton numbering, 8 values per node:
+ * {m, cm_x, cm_y, cm_z, alpha_n, eps_n, e_n, m_ion}; m in n_H x cells,
+ * positions in cells from the box corner, alpha/eps in photons s^-1,
+ * e_n in erg cm^-3 x cells.  out8 is a device array of n_nodes x 8. */
+tr_status tr_tree_nodes(const tr_tree* t, double* out8, tr_stream stream);
+
+/* Sizes of a tr_rays: targets, N_PIX, N_R, accepted-id capacity per target. */
+tr_status tr_rays_info(const tr_rays* r, int64_t* n_targets, int32_t* npix, int32_t* nr,
+                       int32_t* acc_cap);
+
+/* Ray bins as FP64 [n_targets][N_PIX][N_R] (device; NULL skips): alpha and
+ * eps in photons s^-1, e in erg cm^-3 x cells.  ids: [n_targets][acc_cap]
+ * accepted node ids (int64, unordered), counts: [n_targets] (int32). */
+tr_status tr_rays_export(const tr_rays* r, double* alpha, double* eps, double* e,
+                         int64_t* ids, int32_t* counts, tr_stream stream);
+
+/* Node->ray table for N_side (Sec. 2.3, built on the device): key count and
+ * total entries (host outputs).  tr_table_export writes offsets (nkeys+1,
+ * int32) and entries (pixel, count) as two int32 arrays (device). */
+tr_status tr_table_info(int32_t nside, int32_t* nkeys, int32_t* n_entries);
+tr_status tr_table_export(int32_t nside, int32_t* offsets, int32_t* pix, int32_t* cnt,
+                          tr_stream stream);
+
+void tr_tree_free(tr_tree* t);
+void tr_rays_free(tr_rays* r);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* tr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TREERAY_H */

@@ -1,0 +1,364 @@
+// C ABI of the library: argument checks, handle management, and the order
+// of the kernels for each entry point.  See include/treeray.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "tr_internal.cuh"
+
+namespace tr {
+
+static thread_local char g_err[512] = "";
+
+tr_status set_error(tr_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+tr_status cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TR_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(TR_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return set_error(TR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+namespace {
+
+constexpr double C_LIGHT = 2.99792458e10;   // cm s^-1
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+tr_status check_params(const tr_params* p) {
+    if (!p) return set_error(TR_EINVAL, "params is NULL");
+    if (!(p->theta_lim > 0.0) || !(p->theta_if > 0.0) || !(p->theta_src > 0.0))
+        return set_error(TR_EINVAL, "opening angles must be > 0 (INFINITY disables IF/Src MACs)");
+    if (p->nside != 1 && p->nside != 2 && p->nside != 4 && p->nside != 8)
+        return set_error(TR_EINVAL, "nside must be 1, 2, 4 or 8 (got %d)", p->nside);
+    if (!is_pow2(p->eta_r) || p->eta_r > 8)
+        return set_error(TR_EINVAL, "eta_r must be 1, 2, 4 or 8 (got %d)", p->eta_r);
+    if (!(p->alpha_B > 0.0) || !std::isfinite(p->alpha_B)) return set_error(TR_EINVAL, "alpha_B must be finite and > 0");
+    if (!(p->hnu > 0.0) || !std::isfinite(p->hnu)) return set_error(TR_EINVAL, "hnu must be finite and > 0");
+    if (p->precision != TR_FP64 && p->precision != TR_FP32_SWEEP64)
+        return set_error(TR_EINVAL, "precision must be TR_FP64 or TR_FP32_SWEEP64");
+    if (p->max_iter < 1) return set_error(TR_EINVAL, "max_iter must be >= 1");
+    if (p->delta_mode != 0 && p->delta_mode != 1) return set_error(TR_EINVAL, "delta_mode must be 0 or 1");
+    return TR_OK;
+}
+
+tr_status check_grid(const tr_grid* g, const tr_sources* s) {
+    if (!g) return set_error(TR_EINVAL, "grid is NULL");
+    if (!is_pow2(g->N) || g->N < 8 || g->N > 512)
+        return set_error(TR_EINVAL, "N must be a power of two in [8, 512] (got %d)", g->N);
+    if (!(g->dx > 0.0) || !std::isfinite(g->dx)) return set_error(TR_EINVAL, "dx must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->box_lo[a])) return set_error(TR_EINVAL, "box_lo must be finite");
+    if (!g->n_H) return set_error(TR_EINVAL, "n_H is NULL");
+    if (s && s->n < 0) return set_error(TR_EINVAL, "negative source count");
+    if (s && s->n > 0 && (!s->xyz || !s->Q)) return set_error(TR_EINVAL, "source arrays are NULL");
+    return TR_OK;
+}
+
+template <typename T>
+tr_status dev_alloc(T** p, size_t bytes, const char* what) {
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(TR_ENOMEM, "cannot allocate %zu bytes for %s", bytes, what);
+    }
+    return TR_OK;
+}
+
+void tree_release(tr_tree* t) {
+    if (!t) return;
+    cudaFree(t->nodes);
+    cudaFree(t->sums);
+    cudaFree(t->ndot);
+    cudaFree(t->status);
+    cudaFree(t->counter);
+    sweep_tables_free(&t->sw);
+    delete t;
+}
+
+// Allocate (or reuse) a tree for this grid and parameters, then build it.
+tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tree** inout, cudaStream_t st) {
+    tr_status rc = check_params(p);
+    if (rc == TR_OK) rc = check_grid(g, s);
+    if (rc != TR_OK) return rc;
+    int dev = 0;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice")) != TR_OK) return rc;
+    const int N = g->N;
+    int L = 0;
+    while ((1 << L) < N) ++L;
+    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx : (double)N * std::sqrt(3.0);
+    const int nr = p->eta_r * (int)std::floor(std::sqrt(2.0 * lray)) + 1;      // Eq. 5
+    if (nr > MAX_NR) return set_error(TR_EUNSUPPORTED, "N_R = %d exceeds %d evaluation points", nr, MAX_NR);
+    if (nr < 3) return set_error(TR_EINVAL, "L_ray too short: N_R = %d", nr);
+    const int mode = p->precision;
+    const int64_t n_nodes = level_offset(L + 1);
+    const size_t rec = mode == 0 ? sizeof(NodeF64) : sizeof(NodeF32);
+    const size_t sum_bytes = (size_t)n_nodes * 3 * (mode == 0 ? sizeof(double) : sizeof(float));
+    tr_tree* t = *inout;
+    if (t && (t->N != N || t->mode != mode || t->device != dev)) {
+        tree_release(t);
+        t = nullptr;
+        *inout = nullptr;
+    }
+    if (!t) {
+        t = new tr_tree();
+        t->device = dev;
+        t->N = N; t->L = L; t->mode = mode;
+        t->n_nodes = n_nodes;
+        t->nodes_bytes = (size_t)n_nodes * rec;
+        if ((rc = dev_alloc(&t->nodes, t->nodes_bytes, "tree nodes")) != TR_OK ||
+            (rc = dev_alloc(&t->sums, sum_bytes, "tree build sums")) != TR_OK ||
+            (rc = dev_alloc(&t->ndot, sizeof(double) * (size_t)N * N * N, "cell emission")) != TR_OK ||
+            (rc = dev_alloc(&t->status, 4 * sizeof(int32_t), "status words")) != TR_OK ||
+            (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK) {
+            tree_release(t);
+            return rc;
+        }
+    }
+    t->p = *p;
+    t->use_e = g->e_prev != nullptr;
+    t->nr = nr;
+    t->npix = 12 * p->nside * p->nside;
+    for (int a = 0; a < 3; ++a) t->box_lo[a] = g->box_lo[a];
+    t->dx = g->dx;
+    t->U = p->alpha_B * g->dx * g->dx * g->dx;
+    t->Eu = p->alpha_B * g->dx * p->hnu / C_LIGHT;
+    t->lray = lray;
+    *inout = t;
+    if ((rc = table_get(p->nside, &t->table, st)) != TR_OK) return rc;
+    if ((rc = sweep_tables_make(&t->sw, nr, p->eta_r, p->nside, t->npix, p->zeta_g ? 1 : 0, st)) != TR_OK) return rc;
+    return tree_build(t, g, s, st);
+}
+
+std::mutex g_solve_mu;
+std::map<int, tr_tree*> g_solve_trees;   // per device, reused by tr_solve
+
+__global__ void k_iota(int64_t* v, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
+__global__ void k_export_bins(const double* bins, int64_t n, int nbins, double U, double Eu, double* a, double* e,
+                              double* ee) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nbins) return;
+    const int64_t q = i / nbins, b = i % nbins;
+    const double* in = bins + q * 3 * nbins;
+    if (a) a[i] = in[b] * U;
+    if (e) e[i] = in[nbins + b] * U;
+    if (ee) ee[i] = in[2 * nbins + b] * Eu;
+}
+
+__global__ void k_export_ids(const int32_t* ids, const int32_t* counts, int64_t n, int cap, int64_t* out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * cap) return;
+    const int64_t q = i / cap;
+    const int k = (int)(i % cap);
+    out[i] = (k < counts[q]) ? (int64_t)ids[i] : -1;
+}
+
+__global__ void k_table_split(const uint32_t* off, const uint32_t* ent, int nkeys, int32_t* o, int32_t* pix,
+                              int32_t* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nkeys && o) o[i] = (int32_t)off[i];
+    if (i < (int)off[nkeys]) {
+        if (pix) pix[i] = (int32_t)(ent[i] >> 16);
+        if (cnt) cnt[i] = (int32_t)(ent[i] & 0xffffu);
+    }
+}
+
+}  // namespace
+}  // namespace tr
+
+using namespace tr;
+
+extern "C" {
+
+void tr_params_default(tr_params* p) {
+    if (!p) return;
+    p->theta_lim = 0.5;
+    p->theta_if = INFINITY;
+    p->theta_src = INFINITY;
+    p->nside = 2;
+    p->eta_r = 2;
+    p->L_ray_cm = 0.0;
+    p->alpha_B = 2.7e-13;
+    p->hnu = 13.6 * 1.602176634e-12;
+    p->eps_lim = 1e-2;
+    p->delta_mode = 0;
+    p->max_iter = 1;
+    p->precision = TR_FP64;
+    p->zeta_g = 1;
+}
+
+const char* tr_last_error(void) { return g_err; }
+
+tr_status tr_build_tree(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tree** out, tr_stream stream) {
+    g_err[0] = '\0';
+    if (!out) return set_error(TR_EINVAL, "out is NULL");
+    return build(g, s, p, out, (cudaStream_t)stream);
+}
+
+tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_targets, tr_rays** out, tr_stream stream) {
+    g_err[0] = '\0';
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!t || !out) return set_error(TR_EINVAL, "tree or out is NULL");
+    const int64_t ncell = (int64_t)t->N * t->N * t->N;
+    if (n_targets < 0 || n_targets > ncell) return set_error(TR_EINVAL, "n_targets out of range");
+    if (!targets && n_targets != ncell) return set_error(TR_EINVAL, "targets NULL requires n_targets = N^3");
+    tr_rays* r = new tr_rays();
+    r->device = t->device;
+    r->n_targets = n_targets;
+    r->npix = t->npix; r->nr = t->nr; r->use_e = t->use_e;
+    r->U = t->U; r->Eu = t->Eu; r->dx = t->dx;
+    r->acc_cap = 4096;
+    const int nbins = t->npix * t->nr;
+    const int64_t nt = n_targets > 0 ? n_targets : 1;
+    tr_status rc;
+    if ((rc = dev_alloc(&r->bins, sizeof(double) * 3 * nbins * (size_t)nt, "ray bins")) != TR_OK ||
+        (rc = dev_alloc(&r->ids, sizeof(int32_t) * (size_t)r->acc_cap * nt, "accepted ids")) != TR_OK ||
+        (rc = dev_alloc(&r->counts, sizeof(int32_t) * (size_t)nt, "accepted counts")) != TR_OK ||
+        (rc = dev_alloc(&r->eps_self, sizeof(double) * (size_t)nt, "own emission")) != TR_OK ||
+        (rc = dev_alloc(&r->target_idx, sizeof(int64_t) * (size_t)nt, "targets")) != TR_OK) {
+        tr_rays_free(r);
+        return rc;
+    }
+    if (targets) rc = cuda_check(cudaMemcpyAsync(r->target_idx, targets, sizeof(int64_t) * n_targets,
+                                                 cudaMemcpyDeviceToDevice, st), "copy targets");
+    else { k_iota<<<(unsigned)((n_targets + 255) / 256), 256, 0, st>>>(r->target_idx, n_targets); rc = cuda_check(cudaGetLastError(), "iota"); }
+    if (rc == TR_OK) rc = sweep_tables_make(&r->sw, t->nr, t->p.eta_r, t->p.nside, t->npix, t->p.zeta_g ? 1 : 0, st);
+    if (rc == TR_OK && n_targets > 0) {
+        WalkOut o;
+        o.bins = r->bins; o.ids = r->ids; o.counts = r->counts; o.eps_self = r->eps_self; o.acc_cap = r->acc_cap;
+        rc = walk_run(t, r->target_idx, n_targets, true, o, st);
+        if (rc == TR_OK) rc = read_status(t, st);
+    }
+    if (rc != TR_OK) { tr_rays_free(r); return rc; }
+    *out = r;
+    return TR_OK;
+}
+
+tr_status tr_ray_sweep(const tr_rays* r, double* F_out, double* e_out, uint8_t* ion_out, tr_stream stream) {
+    g_err[0] = '\0';
+    if (!r) return set_error(TR_EINVAL, "rays is NULL");
+    if (r->n_targets == 0) return TR_OK;
+    return sweep_run(r, F_out, e_out, ion_out, (cudaStream_t)stream);
+}
+
+tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p, double* F_out, double* e_out,
+                   uint8_t* ion_out, int32_t* iters_out, double* delta_out, tr_stream stream) {
+    g_err[0] = '\0';
+    cudaStream_t st = (cudaStream_t)stream;
+    tr_status rc = check_params(p);
+    if (rc != TR_OK) return rc;
+    if (p->max_iter > 1) return set_error(TR_EUNSUPPORTED, "max_iter > 1 is not available in this build");
+    int dev = 0;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice")) != TR_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_solve_mu);
+    tr_tree*& t = g_solve_trees[dev];
+    if ((rc = build(g, s, p, &t, st)) != TR_OK) return rc;
+    WalkOut o;
+    o.F = F_out; o.e = e_out; o.ion = ion_out;
+    const int64_t ncell = (int64_t)t->N * t->N * t->N;
+    if ((rc = walk_run(t, nullptr, ncell, false, o, st)) != TR_OK) return rc;
+    if ((rc = read_status(t, st)) != TR_OK) return rc;
+    if (iters_out) *iters_out = 1;
+    if (delta_out) *delta_out = INFINITY;
+    return TR_OK;
+}
+
+tr_status tr_tree_info(const tr_tree* t, int64_t* n_nodes, int32_t* levels, int32_t* nr, int32_t* npix) {
+    g_err[0] = '\0';
+    if (!t) return set_error(TR_EINVAL, "tree is NULL");
+    if (n_nodes) *n_nodes = t->n_nodes;
+    if (levels) *levels = t->L + 1;
+    if (nr) *nr = t->nr;
+    if (npix) *npix = t->npix;
+    return TR_OK;
+}
+
+tr_status tr_tree_nodes(const tr_tree* t, double* out8, tr_stream stream) {
+    g_err[0] = '\0';
+    if (!t || !out8) return set_error(TR_EINVAL, "tree or output is NULL");
+    return tree_export(t, out8, (cudaStream_t)stream);
+}
+
+tr_status tr_rays_info(const tr_rays* r, int64_t* n_targets, int32_t* npix, int32_t* nr, int32_t* acc_cap) {
+    g_err[0] = '\0';
+    if (!r) return set_error(TR_EINVAL, "rays is NULL");
+    if (n_targets) *n_targets = r->n_targets;
+    if (npix) *npix = r->npix;
+    if (nr) *nr = r->nr;
+    if (acc_cap) *acc_cap = r->acc_cap;
+    return TR_OK;
+}
+
+tr_status tr_rays_export(const tr_rays* r, double* alpha, double* eps, double* e, int64_t* ids, int32_t* counts,
+                         tr_stream stream) {
+    g_err[0] = '\0';
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!r) return set_error(TR_EINVAL, "rays is NULL");
+    if (r->n_targets == 0) return TR_OK;
+    const int nbins = r->npix * r->nr;
+    const int64_t n = r->n_targets * nbins;
+    if (alpha || eps || e)
+        k_export_bins<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r->bins, r->n_targets, nbins, r->U, r->Eu, alpha, eps, e);
+    if (ids) {
+        const int64_t m = r->n_targets * r->acc_cap;
+        k_export_ids<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(r->ids, r->counts, r->n_targets, r->acc_cap, ids);
+    }
+    tr_status rc = cuda_check(cudaGetLastError(), "export kernels");
+    if (rc == TR_OK && counts)
+        rc = cuda_check(cudaMemcpyAsync(counts, r->counts, sizeof(int32_t) * r->n_targets, cudaMemcpyDeviceToDevice, st),
+                        "copy counts");
+    return rc;
+}
+
+tr_status tr_table_info(int32_t nside, int32_t* nkeys, int32_t* n_entries) {
+    g_err[0] = '\0';
+    if (nside != 1 && nside != 2 && nside != 4 && nside != 8) return set_error(TR_EINVAL, "bad nside %d", nside);
+    const Table* t = nullptr;
+    tr_status rc = table_get(nside, &t, 0);
+    if (rc != TR_OK) return rc;
+    if (nkeys) *nkeys = NKEYS;
+    if (n_entries) *n_entries = t->n_entries;
+    return TR_OK;
+}
+
+tr_status tr_table_export(int32_t nside, int32_t* offsets, int32_t* pix, int32_t* cnt, tr_stream stream) {
+    g_err[0] = '\0';
+    if (nside != 1 && nside != 2 && nside != 4 && nside != 8) return set_error(TR_EINVAL, "bad nside %d", nside);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Table* t = nullptr;
+    tr_status rc = table_get(nside, &t, st);
+    if (rc != TR_OK) return rc;
+    const int n = (t->n_entries > NKEYS + 1) ? t->n_entries : NKEYS + 1;
+    k_table_split<<<(n + 255) / 256, 256, 0, st>>>(t->off, t->ent, NKEYS, offsets, pix, cnt);
+    return cuda_check(cudaGetLastError(), "table export kernel");
+}
+
+void tr_tree_free(tr_tree* t) { tree_release(t); }
+
+void tr_rays_free(tr_rays* r) {
+    if (!r) return;
+    cudaFree(r->bins);
+    cudaFree(r->ids);
+    cudaFree(r->counts);
+    cudaFree(r->eps_self);
+    cudaFree(r->target_idx);
+    sweep_tables_free(&r->sw);
+    delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Internal declarations of the sm_103a TreeRay/OnTheSpot library.
+//
+// Units inside the library (chosen so that FP32 storage neither overflows
+// nor underflows): lengths in cells of the grid, photon rates in units of
+// U = alpha_B dx^3 (so a cell's recombination rate is n_H^2 cells^-3 x U),
+// masses in n_H x cells, energy densities in units of
+// E_u = alpha_B dx h nu / c (so that a beam of flux F carries e = F).
+// Conversions to CGS happen only at the boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/treeray.h"
+
+namespace tr {
+
+// ---- node->ray table definition (Sec. 2.3; the paper's table comes from
+// Paper I and is not reproduced: a node is an axis-aligned cube sampled with
+// TM^3 points, keyed by the integer offset of its geometric centre) ---------
+constexpr int TQH = 16;                     // face bins on either side of the face centre
+constexpr int TQ = 2 * TQH + 1;             // face bins per axis, centre bin included
+constexpr int TB = 40;                      // psi = h/d bins of width 1/32
+constexpr int TM = 8;                       // sample points per cube axis
+constexpr int NKEYS = 6 * TQ * TQ * TB;
+constexpr int MAX_LEVELS = 10;              // N <= 512
+constexpr int MAX_NR = 128;
+constexpr double PI_D = 3.14159265358979323846;
+constexpr double DELTA_IF = 1e-8;           // Sec. 2.4
+
+struct NodeF64 { double cmx, cmy, cmz, m, alpha, eps, e, mion; };   // 64 B
+struct NodeF32 { float cmx, cmy, cmz, m, alpha, eps, e, mion; };    // 32 B
+
+struct Table {                              // CSR: entries of key k are ent[off[k] .. off[k+1])
+    int nside = 0;
+    int n_entries = 0;
+    uint32_t* off = nullptr;                // NKEYS + 1
+    uint32_t* ent = nullptr;                // (pixel << 16) | count
+};
+
+__host__ __device__ inline int64_t level_offset(int l) {
+    return ((int64_t(1) << (3 * l)) - 1) / 7;
+}
+
+__host__ __device__ inline uint32_t spread3(uint32_t v) {   // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ inline uint32_t compact3(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x3ffu;
+    return v;
+}
+__host__ __device__ inline uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ---- host-side handles ---------------------------------------------------
+struct SweepTables {                        // depend on (N_R, eta_R, N_side, N_PIX, zeta_g)
+    int nr = 0, eta = 0, nside = 0, zeta_g = -1;
+    double* r = nullptr;                    // r_i (cells), FP64
+    float* rf = nullptr;                    // r_i, FP32
+    double* inv_r2 = nullptr;               // 1/r_j^2 (0 for j = 0)
+    double* vol = nullptr;                  // ray-cell volume (cells^3), 4pi/N_PIX shells
+    double* G = nullptr;                    // [i][j] dV_ij zeta_g,ij (Eq. 15-16)
+    double* ID2 = nullptr;                  // [i][j] 1/(r_j - r_mid,i)^2
+};
+
+}  // namespace tr
+
+struct tr_tree {
+    int device = 0;
+    int N = 0, L = 0, mode = 0, use_e = 0;
+    int nr = 0, npix = 0;
+    double box_lo[3] = {0, 0, 0}, dx = 0, U = 0, Eu = 0, lray = 0;
+    tr_params p{};
+    int64_t n_nodes = 0;
+    void* nodes = nullptr;                  // NodeF64[n_nodes] or NodeF32[n_nodes]
+    void* sums = nullptr;                   // build scratch: FP64 {smx,smy,smz} or FP32 pairs
+    double* ndot = nullptr;                 // N^3 mapped emission (photons s^-1)
+    int32_t* status = nullptr;              // device status words
+    unsigned int* counter = nullptr;        // persistent-kernel work counter
+    const tr::Table* table = nullptr;
+    tr::SweepTables sw;
+    size_t nodes_bytes = 0;
+};
+
+struct tr_rays {
+    int device = 0;
+    int64_t n_targets = 0;
+    int npix = 0, nr = 0, acc_cap = 0, use_e = 0;
+    double U = 0, Eu = 0, dx = 0;
+    tr::SweepTables sw;                     // borrowed copy of the tree's tables (owned here)
+    double* bins = nullptr;                 // [n_targets][3][npix][nr] scaled units
+    int32_t* ids = nullptr;                 // [n_targets][acc_cap]
+    int32_t* counts = nullptr;              // [n_targets]
+    int64_t* target_idx = nullptr;          // [n_targets] C-order cell indices
+    double* eps_self = nullptr;             // [n_targets] own emission (scaled)
+};
+
+namespace tr {
+
+// error reporting (tr_api.cu)
+tr_status set_error(tr_status st, const char* fmt, ...);
+tr_status cuda_check(cudaError_t e, const char* what);
+
+// table (tr_table.cu)
+tr_status table_get(int nside, const Table** out, cudaStream_t st);
+
+// tree (tr_tree.cu)
+tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStream_t st);
+tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st);
+tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g,
+                            cudaStream_t st);
+void sweep_tables_free(SweepTables* sw);
+
+// walk (tr_walk.cu)
+struct WalkOut {
+    double* F = nullptr;                    // CGS outputs, indexed like the targets
+    double* e = nullptr;
+    uint8_t* ion = nullptr;
+    double* bins = nullptr;                 // dump mode: [target][3][npix][nr]
+    int32_t* ids = nullptr;                 // dump mode: [target][acc_cap]
+    int32_t* counts = nullptr;
+    double* eps_self = nullptr;
+    int acc_cap = 0;
+};
+tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, bool dump,
+                   const WalkOut& out, cudaStream_t st);
+tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st);
+tr_status read_status(const tr_tree* t, cudaStream_t st);
+
+}  // namespace tr

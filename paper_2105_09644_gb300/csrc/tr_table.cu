@@ -1,0 +1,199 @@
+// Node->ray table (Sec. 2.3, first mapping step), built on the device.
+//
+// The paper divides each node between rays in proportion to the volume of
+// the node-ray intersection, read from a table over the node's angular
+// position and angular size (defined in Paper I, not reproduced here).  This
+// table: a node is an axis-aligned cube; its weight in ray k is the fraction
+// of TM^3 sample points of the cube whose direction from the target falls in
+// HEALPix pixel k.  The key is computed from the integer offset between the
+// node's geometric centre and the target centre (in half cells): cube-map
+// face of the dominant axis, a mirror-symmetric bin of each of the other two
+// face coordinates, and the bin floor(32 psi) of psi = node size / centre
+// distance.  Each key's weights are those of a representative cube at
+// distance 1 in the bin's central direction with psi at the bin centre.
+//
+// Storage is CSR: ent[off[k] .. off[k+1]) holds (pixel << 16) | count,
+// sorted by pixel; the weight is count / TM^3.
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "tr_internal.cuh"
+
+namespace tr {
+namespace {
+
+// HEALPix ring-scheme pixel of a direction (Gorski et al. 2005).  Products
+// and sums are rounded one by one (no contraction) so that the sample
+// coordinates and the ring arithmetic are reproducible.
+__device__ int ang2pix_ring(int nside, double x, double y, double z) {
+    const double ns = (double)nside;
+    const int nl4 = 4 * nside, ncap = 2 * nside * (nside - 1), npix = 12 * nside * nside;
+    double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    double zc = __ddiv_rn(z, r);
+    double za = fabs(zc);
+    double phi = atan2(y, x);
+    if (phi < 0.0) phi = __dadd_rn(phi, 2.0 * PI_D);
+    double tt = __ddiv_rn(phi, 0.5 * PI_D);                 // [0, 4]
+    if (tt >= 4.0) tt = __dsub_rn(tt, 4.0);
+    if (za <= 2.0 / 3.0) {
+        double t1 = __dmul_rn(ns, __dadd_rn(0.5, tt));
+        double t2 = __dmul_rn(__dmul_rn(ns, zc), 0.75);
+        long jp = (long)floor(__dsub_rn(t1, t2));            // ascending edge line
+        long jm = (long)floor(__dadd_rn(t1, t2));            // descending edge line
+        long ir = nside + 1 + jp - jm;                       // ring in the belt, 1..2N+1
+        long kshift = 1 - (ir & 1);
+        long num = jp + jm - nside + kshift + 1;
+        long ip = (num >= 0) ? num / 2 : -((-num + 1) / 2);
+        ip %= nl4;
+        if (ip < 0) ip += nl4;
+        return (int)(ncap + (ir - 1) * nl4 + ip);
+    }
+    double tp = __dsub_rn(tt, floor(tt));
+    double tmp = __dmul_rn(ns, __dsqrt_rn(__dmul_rn(3.0, __dsub_rn(1.0, za))));
+    long jp = (long)floor(__dmul_rn(tp, tmp));
+    long jm = (long)floor(__dmul_rn(__dsub_rn(1.0, tp), tmp));
+    long ir = jp + jm + 1;                                   // ring from the nearer pole
+    long ip = (long)floor(__dmul_rn(tt, (double)ir));
+    ip %= 4 * ir;
+    if (ip < 0) ip += 4 * ir;
+    if (zc > 0.0) return (int)(2 * ir * (ir - 1) + ip);
+    return (int)(npix - 2 * ir * (ir + 1) + ip);
+}
+
+__device__ double face_coord(int u) {
+    if (u == TQH) return 0.0;
+    if (u > TQH) return (2.0 * (double)(u - TQH - 1) + 1.0) / (2.0 * TQH);
+    return -(2.0 * (double)(TQH - 1 - u) + 1.0) / (2.0 * TQH);
+}
+
+// Histogram of the key's representative cube over the pixels (block-wide).
+__device__ void key_histogram(int nside, int key, int* hist) {
+    const int npix = 12 * nside * nside;
+    for (int k = threadIdx.x; k < npix; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    int pb = key % TB, rest = key / TB;
+    int v = rest % TQ;
+    rest /= TQ;
+    int u = rest % TQ;
+    int face = rest / TQ;
+    int a = face / 2;
+    int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    double p[3];
+    p[a] = (face & 1) ? -1.0 : 1.0;
+    p[b] = face_coord(u);
+    p[c] = face_coord(v);
+    double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(p[0], p[0]), __dmul_rn(p[1], p[1])),
+                                    __dmul_rn(p[2], p[2])));
+    double C0 = __ddiv_rn(p[0], n), C1 = __ddiv_rn(p[1], n), C2 = __ddiv_rn(p[2], n);
+    double psi = ((double)pb + 0.5) / 32.0;
+    for (int s = threadIdx.x; s < TM * TM * TM; s += blockDim.x) {
+        int ix = s % TM, iy = (s / TM) % TM, iz = s / (TM * TM);
+        double fx = ((double)ix + 0.5) / TM - 0.5;
+        double fy = ((double)iy + 0.5) / TM - 0.5;
+        double fz = ((double)iz + 0.5) / TM - 0.5;
+        double qx = __dadd_rn(C0, __dmul_rn(psi, fx));
+        double qy = __dadd_rn(C1, __dmul_rn(psi, fy));
+        double qz = __dadd_rn(C2, __dmul_rn(psi, fz));
+        atomicAdd(&hist[ang2pix_ring(nside, qx, qy, qz)], 1);
+    }
+    __syncthreads();
+}
+
+__global__ void k_table_count(int nside, uint32_t* counts) {
+    extern __shared__ int hist[];
+    const int key = blockIdx.x;
+    key_histogram(nside, key, hist);
+    const int npix = 12 * nside * nside;
+    int local = 0;
+    for (int k = threadIdx.x; k < npix; k += blockDim.x) local += hist[k] > 0;
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    __shared__ int warp_sum[32];
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_sum[w];
+        counts[key] = (uint32_t)tot;
+    }
+}
+
+// Exclusive scan of n counts into off[0..n] by one block of 1024 threads.
+__global__ void k_scan(const uint32_t* counts, uint32_t* off, int n) {
+    __shared__ uint32_t part[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(n, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < (int)blockDim.x; ++w) { uint32_t t = part[w]; part[w] = run; run += t; }
+        off[n] = run;
+    }
+    __syncthreads();
+    uint32_t run = part[threadIdx.x];
+    for (int i = lo; i < hi; ++i) { off[i] = run; run += counts[i]; }
+}
+
+__global__ void k_table_fill(int nside, const uint32_t* off, uint32_t* ent) {
+    extern __shared__ int hist[];
+    const int key = blockIdx.x;
+    key_histogram(nside, key, hist);
+    if (threadIdx.x == 0) {
+        const int npix = 12 * nside * nside;
+        uint32_t w = off[key];
+        for (int k = 0; k < npix; ++k)
+            if (hist[k] > 0) ent[w++] = ((uint32_t)k << 16) | (uint32_t)hist[k];
+    }
+}
+
+std::mutex g_mu;
+std::map<std::pair<int, int>, Table*> g_tables;
+
+}  // namespace
+
+tr_status table_get(int nside, const Table** out, cudaStream_t st) {
+    int dev = 0;
+    tr_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != TR_OK) return s;
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_tables.find({dev, nside});
+    if (it != g_tables.end()) { *out = it->second; return TR_OK; }
+    Table* t = new Table();
+    t->nside = nside;
+    uint32_t* counts = nullptr;
+    const int npix = 12 * nside * nside;
+    const size_t shm = sizeof(int) * (size_t)npix;
+    if ((s = cuda_check(cudaMalloc(&counts, sizeof(uint32_t) * NKEYS), "cudaMalloc(table counts)")) != TR_OK ||
+        (s = cuda_check(cudaMalloc(&t->off, sizeof(uint32_t) * (NKEYS + 1)), "cudaMalloc(table offsets)")) != TR_OK) {
+        cudaFree(counts);
+        delete t;
+        return s == TR_ECUDA ? TR_ENOMEM : s;
+    }
+    k_table_count<<<NKEYS, 256, shm, st>>>(nside, counts);
+    k_scan<<<1, 1024, 0, st>>>(counts, t->off, NKEYS);
+    uint32_t total = 0;
+    s = cuda_check(cudaMemcpyAsync(&total, t->off + NKEYS, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                   "table size copy");
+    if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "table count kernels");
+    if (s == TR_OK) s = cuda_check(cudaMalloc(&t->ent, sizeof(uint32_t) * (size_t)(total + 1)), "cudaMalloc(table)");
+    if (s == TR_OK) {
+        k_table_fill<<<NKEYS, 256, shm, st>>>(nside, t->off, t->ent);
+        s = cuda_check(cudaStreamSynchronize(st), "table fill kernel");
+    }
+    cudaFree(counts);
+    if (s != TR_OK) {
+        cudaFree(t->off);
+        cudaFree(t->ent);
+        delete t;
+        return s;
+    }
+    t->n_entries = (int)total;
+    g_tables[{dev, nside}] = t;
+    *out = t;
+    return TR_OK;
+}
+
+}  // namespace tr

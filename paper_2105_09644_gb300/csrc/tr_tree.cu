@@ -1,0 +1,254 @@
+// Octree build (Sec. 2.1, Eq. 1-3) with source mapping (Sec. 2.7), and the
+// per-ray constant tables of the sweep (Eq. 4, 15, 16).
+//
+// Layout: nodes of all levels in one array, level-order, Morton order inside
+// a level: node (l, m) has id (8^l - 1)/7 + m and children 8m + c at l + 1
+// (c = x | y << 1 | z << 2), so the eight children of a node are contiguous.
+// Leaves are the cells (level L = log2 N).  Parents are reduced from their
+// children in child order c = 0..7: plain FP64 sums, or FP32
+// Kahan-Neumaier (compensated) sums.
+#include "tr_internal.cuh"
+
+namespace tr {
+namespace {
+
+__global__ void k_ndot_init(double* ndot, const double* ndot_in, int64_t n) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < n) ndot[c] = ndot_in ? ndot_in[c] : 0.0;
+}
+
+// Point sources go to the cell that contains them (radius 0), clamped to the box.
+__global__ void k_map_sources(double* ndot, int N, double lo0, double lo1, double lo2, double dx,
+                              const double* xyz, const double* Q, int n) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double lo[3] = {lo0, lo1, lo2};
+    int64_t ic[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = floor(__ddiv_rn(__dsub_rn(xyz[3 * s + a], lo[a]), dx));
+        f = fmin(fmax(f, 0.0), (double)(N - 1));
+        ic[a] = (int64_t)f;
+    }
+    atomicAdd(&ndot[(ic[2] * N + ic[1]) * N + ic[0]], Q[s]);
+}
+
+struct F32Sum {                              // Kahan-Neumaier accumulator
+    float s = 0.f, c = 0.f;
+    __device__ void add(float x) {
+        float t = s + x;
+        if (fabsf(s) >= fabsf(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ float value() const { return s + c; }
+};
+
+// Leaves (cells): netting of Eq. 1-2 per cell, e of Eq. 3, ionised mass.
+template <int MODE>
+__global__ void k_leaves(void* nodes_v, void* sums_v, int N, int L, const double* n_H,
+                         const double* ndot, const double* e_prev, double invU, double invEu) {
+    const int64_t nleaf = (int64_t)N * N * N;
+    int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= nleaf) return;
+    const uint32_t ix = compact3((uint32_t)m), iy = compact3((uint32_t)m >> 1), iz = compact3((uint32_t)m >> 2);
+    const int64_t c = ((int64_t)iz * N + iy) * N + ix;
+    const int64_t id = level_offset(L) + m;
+    const double n = n_H[c];
+    const double rec = n * n;                       // alpha_B n^2 dV in units of U
+    const double src = ndot[c] * invU;
+    const double ep = e_prev ? e_prev[c] : 0.0;
+    if (MODE == 0) {
+        NodeF64 nd;
+        nd.m = n;
+        double sx = __dmul_rn(n, (double)ix + 0.5), sy = __dmul_rn(n, (double)iy + 0.5),
+               sz = __dmul_rn(n, (double)iz + 0.5);
+        if (n > 0.0) { nd.cmx = __ddiv_rn(sx, n); nd.cmy = __ddiv_rn(sy, n); nd.cmz = __ddiv_rn(sz, n); }
+        else { nd.cmx = (double)ix + 0.5; nd.cmy = (double)iy + 0.5; nd.cmz = (double)iz + 0.5; }
+        nd.alpha = fmax(rec - src, 0.0);
+        nd.eps = fmax(src - rec, 0.0);
+        nd.e = ep * invEu;
+        nd.mion = (ep > 0.0) ? n : 0.0;
+        ((NodeF64*)nodes_v)[id] = nd;
+        double* sm = (double*)sums_v + 3 * id;
+        sm[0] = sx; sm[1] = sy; sm[2] = sz;
+    } else {
+        NodeF32 nd;
+        const float nf = (float)n;
+        nd.m = nf;
+        nd.cmx = (float)ix + 0.5f; nd.cmy = (float)iy + 0.5f; nd.cmz = (float)iz + 0.5f;
+        nd.alpha = (float)fmax(rec - src, 0.0);
+        nd.eps = (float)fmax(src - rec, 0.0);
+        nd.e = (float)(ep * invEu);
+        nd.mion = (ep > 0.0) ? nf : 0.f;
+        ((NodeF32*)nodes_v)[id] = nd;
+        float* sm = (float*)sums_v + 3 * id;
+        sm[0] = nf * nd.cmx; sm[1] = nf * nd.cmy; sm[2] = nf * nd.cmz;
+    }
+}
+
+// One level of parents from their eight contiguous children.
+template <int MODE>
+__global__ void k_parents(void* nodes_v, void* sums_v, int l, int N) {
+    const int64_t nl = int64_t(1) << (3 * l);
+    int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= nl) return;
+    const int64_t id = level_offset(l) + m;
+    const int64_t ch = level_offset(l + 1) + 8 * m;
+    const uint32_t ix = compact3((uint32_t)m), iy = compact3((uint32_t)m >> 1), iz = compact3((uint32_t)m >> 2);
+    const double s = (double)(N >> l);
+    if (MODE == 0) {
+        const NodeF64* c = (const NodeF64*)nodes_v + ch;
+        const double* cs = (const double*)sums_v + 3 * ch;
+        NodeF64 p = c[0];
+        double sx = cs[0], sy = cs[1], sz = cs[2];
+        for (int k = 1; k < 8; ++k) {
+            const NodeF64 q = c[k];
+            p.m = __dadd_rn(p.m, q.m);
+            sx = __dadd_rn(sx, cs[3 * k + 0]);
+            sy = __dadd_rn(sy, cs[3 * k + 1]);
+            sz = __dadd_rn(sz, cs[3 * k + 2]);
+            p.alpha = __dadd_rn(p.alpha, q.alpha);
+            p.eps = __dadd_rn(p.eps, q.eps);
+            p.e = __dadd_rn(p.e, q.e);
+            p.mion = __dadd_rn(p.mion, q.mion);
+        }
+        if (p.m > 0.0) { p.cmx = __ddiv_rn(sx, p.m); p.cmy = __ddiv_rn(sy, p.m); p.cmz = __ddiv_rn(sz, p.m); }
+        else { p.cmx = ((double)ix + 0.5) * s; p.cmy = ((double)iy + 0.5) * s; p.cmz = ((double)iz + 0.5) * s; }
+        ((NodeF64*)nodes_v)[id] = p;
+        double* ps = (double*)sums_v + 3 * id;
+        ps[0] = sx; ps[1] = sy; ps[2] = sz;
+    } else {
+        const NodeF32* c = (const NodeF32*)nodes_v + ch;
+        const float* cs = (const float*)sums_v + 3 * ch;
+        F32Sum m_, sx, sy, sz, al, ep, ee, mi;
+        for (int k = 0; k < 8; ++k) {
+            const NodeF32 q = c[k];
+            m_.add(q.m); al.add(q.alpha); ep.add(q.eps); ee.add(q.e); mi.add(q.mion);
+            sx.add(cs[3 * k + 0]); sy.add(cs[3 * k + 1]); sz.add(cs[3 * k + 2]);
+        }
+        NodeF32 p;
+        p.m = m_.value(); p.alpha = al.value(); p.eps = ep.value(); p.e = ee.value(); p.mion = mi.value();
+        const float fx = sx.value(), fy = sy.value(), fz = sz.value();
+        if (p.m > 0.f) { p.cmx = fx / p.m; p.cmy = fy / p.m; p.cmz = fz / p.m; }
+        else { p.cmx = (float)(((double)ix + 0.5) * s); p.cmy = (float)(((double)iy + 0.5) * s);
+               p.cmz = (float)(((double)iz + 0.5) * s); }
+        ((NodeF32*)nodes_v)[id] = p;
+        float* ps = (float*)sums_v + 3 * id;
+        ps[0] = fx; ps[1] = fy; ps[2] = fz;
+    }
+}
+
+template <int MODE>
+__global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, double Eu) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v[8];
+    if (MODE == 0) {
+        NodeF64 q = ((const NodeF64*)nodes_v)[i];
+        v[0] = q.m; v[1] = q.cmx; v[2] = q.cmy; v[3] = q.cmz;
+        v[4] = q.alpha; v[5] = q.eps; v[6] = q.e; v[7] = q.mion;
+    } else {
+        NodeF32 q = ((const NodeF32*)nodes_v)[i];
+        v[0] = q.m; v[1] = q.cmx; v[2] = q.cmy; v[3] = q.cmz;
+        v[4] = q.alpha; v[5] = q.eps; v[6] = q.e; v[7] = q.mion;
+    }
+    v[4] *= U; v[5] *= U; v[6] *= Eu;
+    for (int k = 0; k < 8; ++k) out[8 * i + k] = v[k];
+}
+
+// Ray constants: r_i (Eq. 4), ray-cell volumes, and for each segment i and
+// source point j > i the loss geometry dV_ij zeta_g,ij (Eq. 15-16) and the
+// inverse square distance from j to the segment midpoint.
+__global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g, double* r, float* rf,
+                               double* inv_r2, double* vol, double* G, double* ID2) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    auto rad = [eta](int i) { return (double)((int64_t)i * i) / (2.0 * (double)eta * (double)eta); };
+    if (t < nr) {
+        const int i = t;
+        const double ri = rad(i);
+        r[i] = ri;
+        rf[i] = (float)ri;
+        inv_r2[i] = (i > 0) ? 1.0 / (ri * ri) : 0.0;
+        const double lo = (i == 0) ? 0.0 : 0.5 * (rad(i - 1) + ri);
+        const double hi = (i == nr - 1) ? ri : 0.5 * (ri + rad(i + 1));
+        vol[i] = (4.0 * PI_D / (double)npix) * (hi * hi * hi - lo * lo * lo) / 3.0;
+    }
+    if (t < nr * nr) {
+        const int i = t / nr, j = t % nr;
+        double g = 0.0, id2 = 0.0;
+        if (j > i && i + 1 < nr) {
+            const double ri = rad(i), ri1 = rad(i + 1), rj = rad(j);
+            const double a = rj - ri, b = rj - ri1;
+            const double dV = (a * a * a - b * b * b) / 3.0;
+            const double zg = zeta_g ? fmin(1.0, (double)nside * (rj - ri) / (2.0 * rj)) : 1.0;
+            g = dV * zg;
+            const double rm = 0.5 * (ri + ri1);
+            id2 = 1.0 / ((rj - rm) * (rj - rm));
+        }
+        G[t] = g;
+        ID2[t] = id2;
+    }
+}
+
+inline unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g,
+                            cudaStream_t st) {
+    if (sw->r && sw->nr == nr && sw->eta == eta && sw->nside == nside && sw->zeta_g == zeta_g) return TR_OK;
+    sweep_tables_free(sw);
+    const size_t n2 = (size_t)nr * nr;
+    tr_status s = TR_OK;
+    if (cudaMalloc(&sw->r, sizeof(double) * nr) != cudaSuccess ||
+        cudaMalloc(&sw->rf, sizeof(float) * nr) != cudaSuccess ||
+        cudaMalloc(&sw->inv_r2, sizeof(double) * nr) != cudaSuccess ||
+        cudaMalloc(&sw->vol, sizeof(double) * nr) != cudaSuccess ||
+        cudaMalloc(&sw->G, sizeof(double) * n2) != cudaSuccess ||
+        cudaMalloc(&sw->ID2, sizeof(double) * n2) != cudaSuccess) {
+        cudaGetLastError();
+        sweep_tables_free(sw);
+        return set_error(TR_ENOMEM, "cannot allocate the ray tables (N_R = %d)", nr);
+    }
+    k_sweep_tables<<<grid_for((int64_t)n2, 128), 128, 0, st>>>(nr, eta, nside, npix, zeta_g, sw->r, sw->rf,
+                                                                sw->inv_r2, sw->vol, sw->G, sw->ID2);
+    s = cuda_check(cudaGetLastError(), "ray table kernel");
+    if (s != TR_OK) return s;
+    sw->nr = nr; sw->eta = eta; sw->nside = nside; sw->zeta_g = zeta_g;
+    return TR_OK;
+}
+
+void sweep_tables_free(SweepTables* sw) {
+    cudaFree(sw->r); cudaFree(sw->rf); cudaFree(sw->inv_r2); cudaFree(sw->vol);
+    cudaFree(sw->G); cudaFree(sw->ID2);
+    *sw = SweepTables();
+}
+
+tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStream_t st) {
+    const int64_t ncell = (int64_t)t->N * t->N * t->N;
+    const double invU = 1.0 / t->U, invEu = 1.0 / t->Eu;
+    k_ndot_init<<<grid_for(ncell, 256), 256, 0, st>>>(t->ndot, g->ndot, ncell);
+    if (s && s->n > 0)
+        k_map_sources<<<grid_for(s->n, 128), 128, 0, st>>>(t->ndot, t->N, g->box_lo[0], g->box_lo[1],
+                                                           g->box_lo[2], g->dx, s->xyz, s->Q, s->n);
+    if (t->mode == 0)
+        k_leaves<0><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->L, g->n_H, t->ndot,
+                                                         g->e_prev, invU, invEu);
+    else
+        k_leaves<1><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->L, g->n_H, t->ndot,
+                                                         g->e_prev, invU, invEu);
+    for (int l = t->L - 1; l >= 0; --l) {
+        const int64_t nl = int64_t(1) << (3 * l);
+        if (t->mode == 0) k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N);
+        else k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N);
+    }
+    return cuda_check(cudaGetLastError(), "tree build kernels");
+}
+
+tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st) {
+    if (t->mode == 0) k_export<0><<<grid_for(t->n_nodes, 256), 256, 0, st>>>(t->nodes, t->n_nodes, out8, t->U, t->Eu);
+    else k_export<1><<<grid_for(t->n_nodes, 256), 256, 0, st>>>(t->nodes, t->n_nodes, out8, t->U, t->Eu);
+    return cuda_check(cudaGetLastError(), "node export kernel");
+}
+
+}  // namespace tr

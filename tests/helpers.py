@@ -1,0 +1,38 @@
+"""Shared helpers of the tests (no method arithmetic)."""
+import numpy as np
+
+
+def interior_mask(ion):
+    """Cells whose six face neighbours share their ionised/neutral class,
+    i.e. cells that are not within one cell of an ionisation front."""
+    ion = np.asarray(ion)
+    m = np.ones(ion.shape, dtype=bool)
+    for ax in range(3):
+        for sh in (1, -1):
+            nb = np.roll(ion, sh, axis=ax)
+            edge = [slice(None)] * 3
+            edge[ax] = 0 if sh == 1 else -1
+            same = nb == ion
+            same[tuple(edge)] = True
+            m &= same
+    return m
+
+
+def near_front(ion_a, ion_b):
+    """Cells where two classifications differ must lie within one cell of
+    the front of the reference classification."""
+    return ~interior_mask(ion_a)
+
+
+def decode_id(cid):
+    level, off = 0, 0
+    while cid >= off + 8 ** level:
+        off += 8 ** level
+        level += 1
+    m = cid - off
+    ix = iy = iz = 0
+    for b in range(level):
+        ix |= ((m >> (3 * b)) & 1) << b
+        iy |= ((m >> (3 * b + 1)) & 1) << b
+        iz |= ((m >> (3 * b + 2)) & 1) << b
+    return level, ix, iy, iz
