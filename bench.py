@@ -1,0 +1,369 @@
+"""Benchmark of the TreeRay/OnTheSpot hot path on GB300.
+
+One step = one pass of the whole hot path over the turbulent-cloud workload
+(128^3 cells, 10 point sources, N_PIX = 48, theta_lim = 0.5): source mapping,
+per-cell netting and tree build (tr_build_tree), then walk + node->ray
+mapping + far-to-near sweep + sum over rays for every cell (tr_walk_sweep).
+The headline `value` is target-cell-rays/s of the FP32-moments + FP64-sweep
+form with inputs resident in HBM; the plain FP64 form is timed beside it.
+`e2e` is the same metric through tr_solve with host buffers (host->device
+copy of the inputs and device->host copy of the flux inside the timed
+region).  The CPU oracle is timed on a bounded sample of the same workload.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank solves its own copy of the workload (independent
+problems, weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "target-cell-rays/s at N_PIX=48 (FP32+FP64-sweep vs plain FP64); p50/p99 latency"
+UNIT = "cell-rays/s"
+WORKLOAD = "turbulent128"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-sample", type=int, default=3000, help="targets in the CPU-oracle sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def _oracle_worker(args):
+    name, targets = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from workloads import workload
+    w = workload(name)
+    t = oracle.Tree(w)
+    p = oracle.params_for(w)
+    t0 = time.perf_counter()
+    t.solve_pass(p, targets=targets)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(name, n_targets, pool):
+    """Oracle walk + map + sweep on a seeded random sample of targets, split
+    over the host cores; the tree build of each worker is not timed."""
+    import numpy as np
+    from workloads import workload
+    w = workload(name)
+    rng = np.random.default_rng(2105)
+    targets = np.sort(rng.choice(w.N ** 3, size=n_targets, replace=False)).astype(np.int64)
+    nproc = pool._processes if pool is not None else 1
+    chunks = [(name, c) for c in np.array_split(targets, nproc)]
+    t0 = time.perf_counter()
+    if pool is None:
+        times = [_oracle_worker(chunks[0])]
+    else:
+        times = pool.map(_oracle_worker, chunks)
+    wall = max(times)
+    return dict(value=n_targets * w.npix / wall, unit=UNIT, cores=nproc, kind="oracle",
+                sample=f"{n_targets} seeded random target cells of {name} ({w.N}^3, N_PIX={w.npix}), "
+                       f"FP64 oracle walk+map+sweep, split over {nproc} processes; tree build not timed",
+                seconds=wall, wall_total=time.perf_counter() - t0)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def walk_traffic(kernel_src_sha):
+    """DRAM bytes of one walk launch from the committed ncu summary, if it was
+    taken on the current walk kernel source."""
+    path = os.path.join(ROOT, "profiles", "walk_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha256") != kernel_src_sha:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    devn = torch.device("cuda", local)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+
+    import paper_2105_09644_gb300 as pkg
+    pkg.build()
+    from paper_2105_09644_gb300 import binding as B
+    from workloads import workload
+
+    w = workload(args.workload)
+    N = w.N
+    ncell = N ** 3
+    units = ncell * w.npix                               # cell-rays per step
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+            for k, v in (("n_H", w.n_H), ("xyz", w.src_xyz), ("Q", w.src_Q))}
+    d = {k: v.to(devn) for k, v in host.items()}
+    F = torch.empty((N, N, N), dtype=torch.float64, device=devn)
+    E = torch.empty_like(F)
+    ion = torch.empty((N, N, N), dtype=torch.uint8, device=devn)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devn)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    grid = B.make_grid(d["n_H"], w.dx)
+    src = B.make_sources(d["xyz"], d["Q"])
+
+    def params(prec):
+        return B.tr_params_default(theta_lim=w.theta_lim, theta_if=w.theta_if, theta_src=w.theta_src,
+                                   nside=w.nside, eta_r=w.eta_r, alpha_B=w.alpha_B, hnu=w.hnu,
+                                   precision=prec)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed_device(prec, steps, warmup, sampler=None):
+        p = params(prec)
+        tree = B.Tree()
+        for _ in range(warmup):
+            B.tr_build_tree(grid, src, p, tree)
+            B.tr_walk_sweep(tree, F, E, ion)
+        barrier()
+        step_ms, walk_ms = [], []
+        t_all = time.perf_counter()
+        for _ in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            B.tr_build_tree(grid, src, p, tree)
+            ev[1].record(stream)
+            B.tr_walk_sweep(tree, F, E, ion)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[2]))
+            walk_ms.append(ev[1].elapsed_time(ev[2]))
+        barrier()
+        wall = time.perf_counter() - t_all
+        stats = B.tr_tree_stats(tree)
+        info = tree.info()
+        return dict(step_ms=step_ms, walk_ms=walk_ms, stats=stats, info=info, wall=wall)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=devn)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # headline: FP32 moments + FP64 sweep, inputs resident
+    with ClockSampler(local) as clk:
+        r32 = timed_device(B.TR_FP32_SWEEP64, args.steps, args.warmup)
+    total_ms = max_over_ranks(sum(r32["step_ms"]))
+    ms_per_step = total_ms / args.steps
+    value = world * units * args.steps / (total_ms * 1e-3)
+
+    # plain FP64 beside it
+    k64 = args.fp64_steps if args.fp64_steps is not None else max(2, min(args.steps, 3))
+    r64 = timed_device(B.TR_FP64, k64, max(1, min(args.warmup, 2)))
+    ms64 = max_over_ranks(sum(r64["step_ms"])) / k64
+
+    # end to end through tr_solve with host buffers
+    p32 = params(B.TR_FP32_SWEEP64)
+    F_host = torch.empty((N, N, N), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        for k in d:
+            d[k].copy_(host[k], non_blocking=True)
+        B.tr_solve(grid, src, p32, F, E, ion)
+        F_host.copy_(F, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(s0.elapsed_time(s1))
+    e2e_total = max_over_ranks(sum(e2e_ms))
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = F_host.numel() * F_host.element_size()
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (walk + map + sweep)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    st = r32["stats"]
+    rec = 32
+    alg_bytes = st["visited"] * rec + st["accepted"] * 8 + st["entries"] * 4 + ncell * (8 + 8 + 1)
+    walk_s = statistics.mean(r32["walk_ms"]) * 1e-3
+    achieved = alg_bytes / walk_s / 1e9
+    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2105_09644_gb300", "csrc", "tr_walk.cu"), "rb").read()).hexdigest()
+    traffic = walk_traffic(src_sha)
+    launches_per_step = 3 + (int(math.log2(N)) - 0) + 1   # ndot init, sources, leaves, L parent levels, walk
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {N}^3 log-normal (sigma_ln 1.5, k^-4), box 10 pc, "
+                               f"{len(w.src_Q)} point sources, N_PIX={w.npix}, N_R={r32['info']['nr']}, "
+                               f"theta_lim={w.theta_lim}",
+                   "precision": "FP32 node moments + compensated FP32 deposits, FP64 sweep",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"independent problem per GPU x{world}"},
+        "latency_ms": {"p50": statistics.median(r32["step_ms"]),
+                       "p99": sorted(r32["step_ms"])[min(len(r32["step_ms"]) - 1, int(math.ceil(0.99 * len(r32["step_ms"]))) - 1)]},
+        "plain_fp64": {"value": world * units / (ms64 * 1e-3), "ms_per_step": ms64,
+                       "p50_ms": statistics.median(r64["step_ms"]), "p99_ms": max(r64["step_ms"]),
+                       "walk_ms": statistics.mean(r64["walk_ms"])},
+        "e2e": {"value": world * units * args.steps / (e2e_total * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_total / args.steps, "api": "tr_solve"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_walk (walk + map + sweep, FP32 moments)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "walk_ms": statistics.mean(r32["walk_ms"]),
+                     "peak_source": f"{peak_src} hbm_gbs",
+                     "counters": st},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if pool is not None:
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample, pool)
+        pool.close()
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step a bounded sample
+    of the workload's targets."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    n = max(256, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, 64, pool)
+    vals, times = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(args.workload, n, pool)
+        vals.append(r["value"])
+        times.append(r["seconds"])
+    pool.close()
+    value = statistics.mean(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.workload} (oracle on a {n}-target sample per step)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                            "sample": r["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

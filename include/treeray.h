@@ -126,6 +126,13 @@ tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_target
 tr_status tr_ray_sweep(const tr_rays* r, double* F_out, double* e_out, uint8_t* ion_out,
                        tr_stream stream);
 
+/* Walk + map + sweep for every cell of a built tree in one fused kernel
+ * (Sec. 2.3-2.5, Eq. 18): the ray bins of each target stay in shared memory.
+ * Outputs as in tr_ray_sweep, N^3 device arrays in C order (NULL allowed).
+ * Synchronises `stream`.  Errors: TR_EINVAL, TR_ECUDA, TR_EOVERFLOW. */
+tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t* ion_out,
+                        tr_stream stream);
+
 /* The fused fast path: build + walk + map + sweep for every cell, repeated
  * (Sec. 2.6) until delta < eps_lim or max_iter passes.  Outputs are N^3
  * device arrays (NULL allowed): F_out, e_out, ion_out as in tr_ray_sweep.
@@ -141,6 +148,10 @@ tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p,
 /* Sizes of a tree: node count, levels (log2 N + 1), N_R, N_PIX. Host outputs. */
 tr_status tr_tree_info(const tr_tree* t, int64_t* n_nodes, int32_t* levels,
                        int32_t* nr, int32_t* npix);
+
+/* Counters of the last walk over this tree (host output, 4 values):
+ * nodes visited, nodes accepted, table entries read, deepest stack. */
+tr_status tr_tree_stats(const tr_tree* t, int64_t* out4);
 
 /* Node records as FP64 in level-order Morton numbering, 8 values per node:
  * {m, cm_x, cm_y, cm_z, alpha_n, eps_n, e_n, m_ion}; m in n_H x cells,

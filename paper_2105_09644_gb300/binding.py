@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_EINVAL", 2: "TR_ENOMEM", 3: "TR_ECUDA", 4: "T
                 5: "TR_EUNSUPPORTED", 6: "TR_EOVERFLOW"}
 
 # every symbol include/treeray.h declares
-EXPORTED = ["tr_params_default", "tr_build_tree", "tr_walk_map", "tr_ray_sweep", "tr_solve",
+EXPORTED = ["tr_params_default", "tr_build_tree", "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve",
+            "tr_tree_stats",
             "tr_tree_info", "tr_tree_nodes", "tr_rays_info", "tr_rays_export", "tr_table_info",
             "tr_table_export", "tr_tree_free", "tr_rays_free", "tr_last_error"]
 
@@ -66,6 +67,8 @@ def load():
     L.tr_build_tree.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), C.POINTER(vp), vp]
     L.tr_walk_map.argtypes = [vp, vp, i64, C.POINTER(vp), vp]
     L.tr_ray_sweep.argtypes = [vp, vp, vp, vp, vp]
+    L.tr_walk_sweep.argtypes = [vp, vp, vp, vp, vp]
+    L.tr_tree_stats.argtypes = [vp, C.POINTER(i64)]
     L.tr_solve.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), vp, vp, vp,
                            C.POINTER(i32), C.POINTER(C.c_double), vp]
     L.tr_tree_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
@@ -182,6 +185,16 @@ def tr_walk_map(tree: Tree, targets=None, n_targets: int | None = None, stream=N
 
 def tr_ray_sweep(rays: Rays, F=None, e=None, ion=None, stream=None):
     check(load().tr_ray_sweep(rays.h, _ptr(F), _ptr(e), _ptr(ion), _stream(stream)))
+
+
+def tr_walk_sweep(tree: Tree, F=None, e=None, ion=None, stream=None):
+    check(load().tr_walk_sweep(tree.h, _ptr(F), _ptr(e), _ptr(ion), _stream(stream)))
+
+
+def tr_tree_stats(tree: Tree) -> dict:
+    out = (C.c_int64 * 4)()
+    check(load().tr_tree_stats(tree.h, out))
+    return dict(visited=out[0], accepted=out[1], entries=out[2], max_stack=out[3])
 
 
 def tr_solve(grid: Grid, sources: Sources, params: Params, F=None, e=None, ion=None, stream=None):

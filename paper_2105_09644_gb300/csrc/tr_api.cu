@@ -82,6 +82,7 @@ void tree_release(tr_tree* t) {
     cudaFree(t->sums);
     cudaFree(t->ndot);
     cudaFree(t->status);
+    cudaFree(t->stats);
     cudaFree(t->counter);
     sweep_tables_free(&t->sw);
     delete t;
@@ -121,6 +122,7 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
             (rc = dev_alloc(&t->sums, sum_bytes, "tree build sums")) != TR_OK ||
             (rc = dev_alloc(&t->ndot, sizeof(double) * (size_t)N * N * N, "cell emission")) != TR_OK ||
             (rc = dev_alloc(&t->status, 4 * sizeof(int32_t), "status words")) != TR_OK ||
+            (rc = dev_alloc(&t->stats, 4 * sizeof(unsigned long long), "walk counters")) != TR_OK ||
             (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK) {
             tree_release(t);
             return rc;
@@ -149,15 +151,21 @@ __global__ void k_iota(int64_t* v, int64_t n) {
     if (i < n) v[i] = i;
 }
 
-__global__ void k_export_bins(const double* bins, int64_t n, int nbins, double U, double Eu, double* a, double* e,
-                              double* ee) {
+__device__ double raw_bin(const double* slot, int mode, float scale) {
+    if (mode == 0) return *slot;
+    const uint2 v = *reinterpret_cast<const uint2*>(slot);
+    return ((double)v.y * 4294967296.0 + (double)v.x) / (double)scale;
+}
+
+__global__ void k_export_bins(const double* bins, int64_t n, int nbins, int mode, const float* sc, double U, double Eu,
+                              double* a, double* e, double* ee) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n * nbins) return;
     const int64_t q = i / nbins, b = i % nbins;
     const double* in = bins + q * 3 * nbins;
-    if (a) a[i] = in[b] * U;
-    if (e) e[i] = in[nbins + b] * U;
-    if (ee) ee[i] = in[2 * nbins + b] * Eu;
+    if (a) a[i] = raw_bin(in + b, mode, sc[0]) * U;
+    if (e) e[i] = raw_bin(in + nbins + b, mode, sc[1]) * U;
+    if (ee) ee[i] = raw_bin(in + 2 * nbins + b, mode, sc[2]) * Eu;
 }
 
 __global__ void k_export_ids(const int32_t* ids, const int32_t* counts, int64_t n, int cap, int64_t* out) {
@@ -220,7 +228,7 @@ tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_target
     tr_rays* r = new tr_rays();
     r->device = t->device;
     r->n_targets = n_targets;
-    r->npix = t->npix; r->nr = t->nr; r->use_e = t->use_e;
+    r->npix = t->npix; r->nr = t->nr; r->use_e = t->use_e; r->mode = t->mode;
     r->U = t->U; r->Eu = t->Eu; r->dx = t->dx;
     r->acc_cap = 4096;
     const int nbins = t->npix * t->nr;
@@ -230,7 +238,8 @@ tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_target
         (rc = dev_alloc(&r->ids, sizeof(int32_t) * (size_t)r->acc_cap * nt, "accepted ids")) != TR_OK ||
         (rc = dev_alloc(&r->counts, sizeof(int32_t) * (size_t)nt, "accepted counts")) != TR_OK ||
         (rc = dev_alloc(&r->eps_self, sizeof(double) * (size_t)nt, "own emission")) != TR_OK ||
-        (rc = dev_alloc(&r->target_idx, sizeof(int64_t) * (size_t)nt, "targets")) != TR_OK) {
+        (rc = dev_alloc(&r->target_idx, sizeof(int64_t) * (size_t)nt, "targets")) != TR_OK ||
+        (rc = dev_alloc(&r->scales, 4 * sizeof(float), "bin scales")) != TR_OK) {
         tr_rays_free(r);
         return rc;
     }
@@ -241,6 +250,7 @@ tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_target
     if (rc == TR_OK && n_targets > 0) {
         WalkOut o;
         o.bins = r->bins; o.ids = r->ids; o.counts = r->counts; o.eps_self = r->eps_self; o.acc_cap = r->acc_cap;
+        o.scales = r->scales;
         rc = walk_run(t, r->target_idx, n_targets, true, o, st);
         if (rc == TR_OK) rc = read_status(t, st);
     }
@@ -254,6 +264,29 @@ tr_status tr_ray_sweep(const tr_rays* r, double* F_out, double* e_out, uint8_t* 
     if (!r) return set_error(TR_EINVAL, "rays is NULL");
     if (r->n_targets == 0) return TR_OK;
     return sweep_run(r, F_out, e_out, ion_out, (cudaStream_t)stream);
+}
+
+tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t* ion_out, tr_stream stream) {
+    g_err[0] = '\0';
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!t) return set_error(TR_EINVAL, "tree is NULL");
+    WalkOut o;
+    o.F = F_out; o.e = e_out; o.ion = ion_out;
+    tr_status rc = walk_run(t, nullptr, (int64_t)t->N * t->N * t->N, false, o, st);
+    if (rc == TR_OK) rc = read_status(t, st);
+    return rc;
+}
+
+tr_status tr_tree_stats(const tr_tree* t, int64_t* out4) {
+    g_err[0] = '\0';
+    if (!t || !out4) return set_error(TR_EINVAL, "tree or output is NULL");
+    unsigned long long h[4] = {0, 0, 0, 0};
+    int32_t st[4] = {0, 0, 0, 0};
+    tr_status rc = cuda_check(cudaMemcpy(h, t->stats, sizeof h, cudaMemcpyDeviceToHost), "stats copy");
+    if (rc == TR_OK) rc = cuda_check(cudaMemcpy(st, t->status, sizeof st, cudaMemcpyDeviceToHost), "status copy");
+    if (rc != TR_OK) return rc;
+    out4[0] = (int64_t)h[0]; out4[1] = (int64_t)h[1]; out4[2] = (int64_t)h[2]; out4[3] = st[1];
+    return TR_OK;
 }
 
 tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p, double* F_out, double* e_out,
@@ -313,7 +346,8 @@ tr_status tr_rays_export(const tr_rays* r, double* alpha, double* eps, double* e
     const int nbins = r->npix * r->nr;
     const int64_t n = r->n_targets * nbins;
     if (alpha || eps || e)
-        k_export_bins<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r->bins, r->n_targets, nbins, r->U, r->Eu, alpha, eps, e);
+        k_export_bins<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r->bins, r->n_targets, nbins, r->mode, r->scales,
+                                                                   r->U, r->Eu, alpha, eps, e);
     if (ids) {
         const int64_t m = r->n_targets * r->acc_cap;
         k_export_ids<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(r->ids, r->counts, r->n_targets, r->acc_cap, ids);
@@ -357,6 +391,7 @@ void tr_rays_free(tr_rays* r) {
     cudaFree(r->counts);
     cudaFree(r->eps_self);
     cudaFree(r->target_idx);
+    cudaFree(r->scales);
     sweep_tables_free(&r->sw);
     delete r;
 }

@@ -36,6 +36,7 @@ struct Table {                              // CSR: entries of key k are ent[off
     int n_entries = 0;
     uint32_t* off = nullptr;                // NKEYS + 1
     uint32_t* ent = nullptr;                // (pixel << 16) | count
+    uint2* hdr = nullptr;                   // NKEYS x {off[k], number of entries}: one load per key
 };
 
 __host__ __device__ inline int64_t level_offset(int l) {
@@ -68,9 +69,14 @@ struct SweepTables {                        // depend on (N_R, eta_R, N_side, N_
     double* r = nullptr;                    // r_i (cells), FP64
     float* rf = nullptr;                    // r_i, FP32
     double* inv_r2 = nullptr;               // 1/r_j^2 (0 for j = 0)
-    double* vol = nullptr;                  // ray-cell volume (cells^3), 4pi/N_PIX shells
+    double* inv_vol = nullptr;              // 1 / ray-cell volume (cells^-3), 4pi/N_PIX shells
+    float* inv_volf = nullptr;              // the same in FP32
     double* G = nullptr;                    // [i][j] dV_ij zeta_g,ij (Eq. 15-16)
     double* ID2 = nullptr;                  // [i][j] 1/(r_j - r_mid,i)^2
+    double* GI = nullptr;                   // [i][j] G_ij ID2_ij
+    float* Gf = nullptr;                    // FP32 copies of G, ID2, GI
+    float* ID2f = nullptr;
+    float* GIf = nullptr;
 };
 
 }  // namespace tr
@@ -85,7 +91,8 @@ struct tr_tree {
     void* nodes = nullptr;                  // NodeF64[n_nodes] or NodeF32[n_nodes]
     void* sums = nullptr;                   // build scratch: FP64 {smx,smy,smz} or FP32 pairs
     double* ndot = nullptr;                 // N^3 mapped emission (photons s^-1)
-    int32_t* status = nullptr;              // device status words
+    int32_t* status = nullptr;              // device status words: [0] overflowed targets, [1] deepest stack
+    unsigned long long* stats = nullptr;    // device counters of the last walk: visited, accepted, entries
     unsigned int* counter = nullptr;        // persistent-kernel work counter
     const tr::Table* table = nullptr;
     tr::SweepTables sw;
@@ -95,10 +102,11 @@ struct tr_tree {
 struct tr_rays {
     int device = 0;
     int64_t n_targets = 0;
-    int npix = 0, nr = 0, acc_cap = 0, use_e = 0;
+    int npix = 0, nr = 0, acc_cap = 0, use_e = 0, mode = 0;
+    float* scales = nullptr;                // FP32 form: fixed-point units of the raw bins
     double U = 0, Eu = 0, dx = 0;
     tr::SweepTables sw;                     // borrowed copy of the tree's tables (owned here)
-    double* bins = nullptr;                 // [n_targets][3][npix][nr] scaled units
+    double* bins = nullptr;                 // [n_targets][3][npix][nr] raw bins (FP64, or FP32-form fixed point)
     int32_t* ids = nullptr;                 // [n_targets][acc_cap]
     int32_t* counts = nullptr;              // [n_targets]
     int64_t* target_idx = nullptr;          // [n_targets] C-order cell indices
@@ -130,6 +138,7 @@ struct WalkOut {
     int32_t* ids = nullptr;                 // dump mode: [target][acc_cap]
     int32_t* counts = nullptr;
     double* eps_self = nullptr;
+    float* scales = nullptr;
     int acc_cap = 0;
 };
 tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, bool dump,

@@ -149,6 +149,11 @@ __global__ void k_table_fill(int nside, const uint32_t* off, uint32_t* ent) {
     }
 }
 
+__global__ void k_table_hdr(const uint32_t* off, uint2* hdr, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) hdr[k] = make_uint2(off[k], off[k + 1] - off[k]);
+}
+
 std::mutex g_mu;
 std::map<std::pair<int, int>, Table*> g_tables;
 
@@ -181,12 +186,17 @@ tr_status table_get(int nside, const Table** out, cudaStream_t st) {
     if (s == TR_OK) s = cuda_check(cudaMalloc(&t->ent, sizeof(uint32_t) * (size_t)(total + 1)), "cudaMalloc(table)");
     if (s == TR_OK) {
         k_table_fill<<<NKEYS, 256, shm, st>>>(nside, t->off, t->ent);
-        s = cuda_check(cudaStreamSynchronize(st), "table fill kernel");
+        s = cuda_check(cudaMalloc(&t->hdr, sizeof(uint2) * NKEYS), "cudaMalloc(table headers)");
+    }
+    if (s == TR_OK) {
+        k_table_hdr<<<(NKEYS + 255) / 256, 256, 0, st>>>(t->off, t->hdr, NKEYS);
+        s = cuda_check(cudaStreamSynchronize(st), "table fill kernels");
     }
     cudaFree(counts);
     if (s != TR_OK) {
         cudaFree(t->off);
         cudaFree(t->ent);
+        cudaFree(t->hdr);
         delete t;
         return s;
     }

@@ -160,7 +160,8 @@ __global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, 
 // source point j > i the loss geometry dV_ij zeta_g,ij (Eq. 15-16) and the
 // inverse square distance from j to the segment midpoint.
 __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g, double* r, float* rf,
-                               double* inv_r2, double* vol, double* G, double* ID2) {
+                               double* inv_r2, double* inv_vol, float* inv_volf, double* G, double* ID2, double* GI,
+                               float* Gf, float* ID2f, float* GIf) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     auto rad = [eta](int i) { return (double)((int64_t)i * i) / (2.0 * (double)eta * (double)eta); };
     if (t < nr) {
@@ -171,7 +172,8 @@ __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g,
         inv_r2[i] = (i > 0) ? 1.0 / (ri * ri) : 0.0;
         const double lo = (i == 0) ? 0.0 : 0.5 * (rad(i - 1) + ri);
         const double hi = (i == nr - 1) ? ri : 0.5 * (ri + rad(i + 1));
-        vol[i] = (4.0 * PI_D / (double)npix) * (hi * hi * hi - lo * lo * lo) / 3.0;
+        inv_vol[i] = 1.0 / ((4.0 * PI_D / (double)npix) * (hi * hi * hi - lo * lo * lo) / 3.0);
+        inv_volf[i] = (float)inv_vol[i];
     }
     if (t < nr * nr) {
         const int i = t / nr, j = t % nr;
@@ -187,6 +189,10 @@ __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g,
         }
         G[t] = g;
         ID2[t] = id2;
+        GI[t] = g * id2;
+        Gf[t] = (float)g;
+        ID2f[t] = (float)id2;
+        GIf[t] = (float)(g * id2);
     }
 }
 
@@ -203,15 +209,21 @@ tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npi
     if (cudaMalloc(&sw->r, sizeof(double) * nr) != cudaSuccess ||
         cudaMalloc(&sw->rf, sizeof(float) * nr) != cudaSuccess ||
         cudaMalloc(&sw->inv_r2, sizeof(double) * nr) != cudaSuccess ||
-        cudaMalloc(&sw->vol, sizeof(double) * nr) != cudaSuccess ||
+        cudaMalloc(&sw->inv_vol, sizeof(double) * nr) != cudaSuccess ||
+        cudaMalloc(&sw->inv_volf, sizeof(float) * nr) != cudaSuccess ||
         cudaMalloc(&sw->G, sizeof(double) * n2) != cudaSuccess ||
-        cudaMalloc(&sw->ID2, sizeof(double) * n2) != cudaSuccess) {
+        cudaMalloc(&sw->ID2, sizeof(double) * n2) != cudaSuccess ||
+        cudaMalloc(&sw->GI, sizeof(double) * n2) != cudaSuccess ||
+        cudaMalloc(&sw->Gf, sizeof(float) * n2) != cudaSuccess ||
+        cudaMalloc(&sw->ID2f, sizeof(float) * n2) != cudaSuccess ||
+        cudaMalloc(&sw->GIf, sizeof(float) * n2) != cudaSuccess) {
         cudaGetLastError();
         sweep_tables_free(sw);
         return set_error(TR_ENOMEM, "cannot allocate the ray tables (N_R = %d)", nr);
     }
     k_sweep_tables<<<grid_for((int64_t)n2, 128), 128, 0, st>>>(nr, eta, nside, npix, zeta_g, sw->r, sw->rf,
-                                                                sw->inv_r2, sw->vol, sw->G, sw->ID2);
+                                                                sw->inv_r2, sw->inv_vol, sw->inv_volf, sw->G, sw->ID2, sw->GI,
+                                                                sw->Gf, sw->ID2f, sw->GIf);
     s = cuda_check(cudaGetLastError(), "ray table kernel");
     if (s != TR_OK) return s;
     sw->nr = nr; sw->eta = eta; sw->nside = nside; sw->zeta_g = zeta_g;
@@ -219,8 +231,8 @@ tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npi
 }
 
 void sweep_tables_free(SweepTables* sw) {
-    cudaFree(sw->r); cudaFree(sw->rf); cudaFree(sw->inv_r2); cudaFree(sw->vol);
-    cudaFree(sw->G); cudaFree(sw->ID2);
+    cudaFree(sw->r); cudaFree(sw->rf); cudaFree(sw->inv_r2); cudaFree(sw->inv_vol); cudaFree(sw->inv_volf);
+    cudaFree(sw->G); cudaFree(sw->ID2); cudaFree(sw->GI); cudaFree(sw->Gf); cudaFree(sw->ID2f); cudaFree(sw->GIf);
     *sw = SweepTables();
 }
 

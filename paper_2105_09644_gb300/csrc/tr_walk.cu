@@ -34,12 +34,18 @@ struct WalkArgs {
     float th_lim2f, th_if2f, th_src2f, lrayf;
     const uint32_t* toff;
     const uint32_t* tent;
+    const uint2* hdr;
     const double* r;
     const float* rf;
     const double* inv_r2;
-    const double* vol;
+    const double* inv_vol;
+    const float* inv_volf;
     const double* G;
     const double* ID2;
+    const double* GI;
+    const float* Gf;
+    const float* ID2f;
+    const float* GIf;
     const int64_t* targets;                 // NULL: all cells, visited in Morton order
     int64_t n_targets;
     double Fconv, Econv;                    // scaled flux -> CGS flux / energy density
@@ -50,16 +56,15 @@ struct WalkArgs {
     int32_t* ids_out;
     int32_t* counts_out;
     double* eps_self_out;
+    float* scales_out;                      // dump: the fixed-point units of the FP32 form
+    const float* scales_in;                 // stored sweep: the same, read back
     int acc_cap;
     int32_t* status;
+    unsigned long long* stats;
     unsigned int* counter;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
@@ -104,27 +109,55 @@ __device__ __forceinline__ int table_key(int ox, int oy, int oz, int s) {
     return ((face * TQ + u) * TQ + v) * TB + (int)pb;
 }
 
-template <int MODE>
-__device__ __forceinline__ void bin_add(double* slot, typename Prec<MODE>::real x) {
-    if (MODE == 0) {
-        *slot += (double)x;
-    } else {
-        float2* p = reinterpret_cast<float2*>(slot);
-        float2 v = *p;
-        const float xf = (float)x;
-        const float t = v.x + xf;
-        if (fabsf(v.x) >= fabsf(xf)) v.y += (v.x - t) + xf;
-        else v.y += (xf - t) + v.x;
-        v.x = t;
-        *p = v;
-    }
+// Ray bins.  FP64 form: one double per bin, atomic FP64 adds.  FP32 form: the
+// FP32 addends are accumulated exactly in 64-bit fixed point, kept as two
+// 32-bit words (low word, high word) updated by two integer atomics with the
+// carry of the low word propagated: an order-independent sum whose only
+// rounding is that of each FP32 addend.  The fixed-point unit is a power of
+// two chosen from the root node's total, so that no bin can exceed 2^62.
+struct Scales { float a, eps, e; };          // fixed-point units per quantity (FP32 form)
+
+__device__ __forceinline__ float fixed_scale(float total) {
+    int ex = 0;
+    frexpf(total > 0.f ? total : 1.f, &ex);   // total < 2^ex
+    return ldexpf(1.0f, min(62 - ex, 126));
 }
 
 template <int MODE>
-__device__ __forceinline__ double bin_value(const double* slot) {
+__device__ __forceinline__ double bin_value(const double* slot, float scale) {
     if (MODE == 0) return *slot;
-    const float2 v = *reinterpret_cast<const float2*>(slot);
-    return (double)v.x + (double)v.y;
+    const uint2 v = *reinterpret_cast<const uint2*>(slot);
+    return ((double)v.y * 4294967296.0 + (double)v.x) / (double)scale;
+}
+
+template <int MODE>
+__device__ __forceinline__ float bin_value_f(const double* slot, float inv_scale) {
+    const uint2 v = *reinterpret_cast<const uint2*>(slot);
+    return ((float)v.y * 4294967296.0f + (float)v.x) * inv_scale;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool bin_nonzero(const double* slot) {
+    if (MODE == 0) return *slot > 0.0;
+    const uint2 v = *reinterpret_cast<const uint2*>(slot);
+    return (v.x | v.y) != 0u;
+}
+
+template <int MODE>
+__device__ __forceinline__ void bin_atomic_add(double* slot, typename Prec<MODE>::real x, float scale) {
+    if (MODE == 0) {
+        atomicAdd(slot, (double)x);
+    } else {
+        const float v = (float)x * scale;                     // exact: scale is a power of two
+        if (!(v > 0.f)) return;
+        const float hf = floorf(v * 2.3283064365386963e-10f);  // v / 2^32, exact
+        const float lf = v - hf * 4294967296.0f;              // exact, < 2^32
+        const unsigned lo = (unsigned)lf, hi = (unsigned)hf;
+        unsigned* w = reinterpret_cast<unsigned*>(slot);
+        const unsigned old = atomicAdd(w, lo);
+        const unsigned carry = (old + lo < old) ? 1u : 0u;
+        if (hi + carry) atomicAdd(w + 1, hi + carry);
+    }
 }
 
 template <int MODE>
@@ -170,187 +203,323 @@ __device__ __forceinline__ float dist2(float tx, float ty, float tz, const float
     return dx * dx + dy * dy + dz * dz;
 }
 
-// Map one accepted node onto the warp's ray bins (all lanes call this with
-// the same, broadcast, arguments).
+// Radial spread of one accepted node (App. A), prepared by the thread that
+// accepted it and applied by the whole CTA, one (node, ray) pair per thread.
+// kind 0: W_p(|r_i - d| / h) / S over points lo .. lo+npts-1 (S = sum over
+// all points); kind 1: everything on one point (node beyond the last point);
+// kind 2: linear split w0, w1 between the two points bracketing d (no point
+// inside the W_p support).
 template <int MODE>
-__device__ void map_node(const WalkArgs& a, double* bins_a, double* bins_eps, double* bins_e,
-                         typename Prec<MODE>::real* wrad, int key, typename Prec<MODE>::real d, int s,
-                         typename Prec<MODE>::real alpha, typename Prec<MODE>::real eps,
-                         typename Prec<MODE>::real e, int lane) {
+struct RadialSpread {
+    typename Prec<MODE>::real d, a, b;      // kind 0/3: d, 1/h, 1/S; kind 2: -, w0, w1
+    typename Prec<MODE>::real alpha, e;
+    uint32_t off;                           // first table entry of the node's key
+    int16_t lo, npts;
+    uint8_t kind, woff;                     // kind 3: raw W_p values kept in the setup thread's row
+    uint16_t src;                           //   of the weight scratch, from column woff
+};
+
+constexpr int MAXW = 12;                    // W_p values kept per node (longer supports recompute)
+
+template <int MODE>
+__device__ __forceinline__ typename Prec<MODE>::real spread_weight(const RadialSpread<MODE>& n, int j,
+                                                                 const typename Prec<MODE>::real* r,
+                                                                 const typename Prec<MODE>::real* wts) {
+    using real = typename Prec<MODE>::real;
+    if (n.kind == 3) return wts[n.src * MAXW + n.woff + j] * n.b;
+    if (n.kind == 0) return wp_kernel<real>(fabs(r[n.lo + j] - n.d) * n.a) * n.b;
+    if (n.kind == 1) return real(1);
+    return j == 0 ? n.a : n.b;
+}
+
+// W_p normalisation of an accepted node: the support of the kernel on the
+// evaluation points and 1/S.
+template <int MODE>
+__device__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename Prec<MODE>::real d, int s,
+                             typename Prec<MODE>::real* wrow) {
     using real = typename Prec<MODE>::real;
     const int nr = a.nr;
-    const real* r = nullptr;
-    if (MODE == 0) r = reinterpret_cast<const real*>(a.r);
-    else r = reinterpret_cast<const real*>(a.rf);
-    const real rlast = r[nr - 1];
-    const uint32_t eo = __ldg(a.toff + key), en = __ldg(a.toff + key + 1) - eo;
-    const real inv_m3 = real(1.0) / real(TM * TM * TM);
-    const bool do_e = a.use_e && e != real(0);
-    if (alpha != real(0) || do_e) {
-        // radial weights W_p(|r_i - d| / h), normalised over the points (App. A)
-        int i0, ni;
-        const real h = (real)s;
-        if (d >= rlast) {
-            i0 = nr - 1; ni = 1;
-            if (lane == 0) wrad[0] = real(1);
+    const real* r = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
+    n.d = d;
+    if (d >= r[nr - 1]) {
+        n.kind = 1; n.lo = (int16_t)(nr - 1); n.npts = 1; n.a = real(1); n.b = real(1);
+        return;
+    }
+    const real h = (real)s, inv_h = real(1) / h;
+    const real reach = real(0.8661) * h;
+    const real dlo = d > reach ? d - reach : real(0);
+    const int lo = max((int)floor((real)a.eta * sqrt(real(2) * dlo)) - 1, 0);
+    const int hi = min((int)ceil((real)a.eta * sqrt(real(2) * (d + reach))) + 1, nr - 1);
+    real S = real(0);
+    int first = hi + 1, last = lo - 1;
+    const bool keep = hi - lo + 1 <= MAXW;
+    for (int i = lo; i <= hi; ++i) {
+        const real w = wp_kernel<real>(fabs(r[i] - d) * inv_h);
+        if (keep) wrow[i - lo] = w;
+        if (w > real(0)) { S += w; first = min(first, i); last = i; }
+    }
+    if (S > real(0)) {
+        n.kind = keep ? 3 : 0; n.woff = (uint8_t)(first - lo);
+        n.lo = (int16_t)first; n.npts = (int16_t)(last - first + 1); n.a = inv_h; n.b = real(1) / S;
+        return;
+    }
+    int i = min(max((int)floor((real)a.eta * sqrt(real(2) * d)), 0), nr - 2);
+    while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
+    while (i > 0 && r[i] > d) --i;
+    const real ra = r[i], rb = r[i + 1];
+    n.kind = 2; n.lo = (int16_t)i; n.npts = 2;
+    n.a = (rb - d) / (rb - ra);
+    n.b = (d - ra) / (rb - ra);
+}
+
+// W_f,3 (App. A.3) deposit of an emitting node: two points r_i <= d < r_{i+1}
+// keeping the sum and the flux at the target exact.  Emitting nodes are few
+// (they contain a source), so the accepting thread does it alone.
+template <int MODE>
+__device__ void deposit_eps(const WalkArgs& a, double* bins_eps, uint32_t off, int ne,
+                            typename Prec<MODE>::real d, typename Prec<MODE>::real eps, float scale) {
+    using real = typename Prec<MODE>::real;
+    const int nr = a.nr;
+    const real* r = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
+    int i;
+    real w0, w1;
+    if (d >= r[nr - 1]) {
+        i = nr - 2; w0 = real(0); w1 = real(1);
+    } else {
+        i = min(max((int)floor((real)a.eta * sqrt(real(2) * d)), 0), nr - 2);
+        while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
+        while (i > 0 && r[i] > d) --i;
+        if (i == 0) {
+            w0 = real(0); w1 = real(1);
         } else {
-            const real reach = real(0.8661) * h;
-            const real dlo = d > reach ? d - reach : real(0);
-            int lo = (int)floor((real)a.eta * sqrt(real(2) * dlo)) - 1;
-            int hi = (int)ceil((real)a.eta * sqrt(real(2) * (d + reach))) + 1;
-            lo = max(lo, 0);
-            hi = min(hi, nr - 1);
-            i0 = lo; ni = hi - lo + 1;
-            real S = real(0);
-            for (int j = lane; j < ni; j += 32) {
-                const real w = wp_kernel<real>(fabs(r[i0 + j] - d) / h);
-                wrad[j] = w;
-                S += w;
-            }
-            S = warp_sum(S);
-            __syncwarp();
-            if (S > real(0)) {
-                for (int j = lane; j < ni; j += 32) wrad[j] = wrad[j] / S;
+            const real ri = r[i], rj = r[i + 1];
+            const real ia = real(1) / (ri * ri), ib = real(1) / (rj * rj), it = real(1) / (d * d);
+            w1 = (ia - it) / (ia - ib);
+            w0 = real(1) - w1;
+        }
+    }
+    const real inv_m3 = real(1.0) / real(TM * TM * TM);
+    for (int k = 0; k < ne; ++k) {
+        const uint32_t en = __ldg(a.tent + off + k);
+        const int b = (int)(en >> 16) * nr + i;
+        const real wk = (real)(en & 0xffffu) * inv_m3;
+        if (w0 != real(0)) bin_atomic_add<MODE>(bins_eps + b, wk * w0 * eps, scale);
+        if (w1 != real(0)) bin_atomic_add<MODE>(bins_eps + b + 1, wk * w1 * eps, scale);
+    }
+}
+
+// 1/a in FP64 by the Newton-Raphson iteration y <- y + y (1 - a y), seeded with
+// the correctly rounded FP32 reciprocal: the relative error squares at each
+// step (2^-23 -> 2^-46 -> below FP64 rounding), two steps suffice.
+__device__ __forceinline__ double recip_nr(double a) {
+    const float af = (float)a;
+    if (!(fabsf(af) > 1e-30f && fabsf(af) < 1e30f)) return 1.0 / a;
+    double y = (double)__frcp_rn(af);
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    return fma(y, e, y);
+}
+
+// Recombination coefficient per unit volume at point i of a ray.  In the
+// FP32 form the deposits are FP32, so the coefficient is formed in FP32 and
+// widened; the photon budget itself (Phi_j and its losses) is FP64.
+template <int MODE>
+__device__ __forceinline__ double alpha_at(const WalkArgs& a, const double* ba, int i, float inv_scale) {
+    if (MODE == 0) return ba[i] * __ldg(a.inv_vol + i);
+    return (double)(bin_value_f<MODE>(ba + i, inv_scale) * __ldg(a.inv_volf + i));
+}
+
+// Far-to-near sweep of one ray (Sec. 2.5) straight from its bins: ba, be, bee
+// are the ray's N_R slots of alpha, eps and e (raw deposits).  Rays without
+// emission cost only the scan for it.  The eps slots are overwritten with the
+// photon rates Phi_j (FP64).
+template <int MODE>
+__device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, const double* bee, const Scales& sc) {
+    const int nr = a.nr;
+    uint64_t m0 = 0, m1 = 0;
+    for (int j = 1; j < nr; ++j) {
+        if (bin_nonzero<MODE>(be + j)) {
+            if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64);
+        }
+    }
+    if (!(m0 | m1)) return 0.0;
+    const double inv4pi = 1.0 / (4.0 * PI_D);
+    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; be[j] = bin_value<MODE>(be + j, sc.eps) * inv4pi; }
+    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; be[j] = bin_value<MODE>(be + j, sc.eps) * inv4pi; }
+    double* ph = be;                                              // Eq. 12
+    const float ia = 1.0f / sc.a, ie = 1.0f / sc.e;
+    const int jtop = m1 ? 64 + 63 - __clzll((long long)m1) : 63 - __clzll((long long)m0);
+    double a_hi = alpha_at<MODE>(a, ba, jtop, ia);
+    for (int i = jtop - 1; i >= 0 && (m0 | m1); --i) {
+        const double a_lo = alpha_at<MODE>(a, ba, i, ia);
+        const int b = i + 1;                                      // sources strictly beyond r_i
+        const uint64_t a0 = (b < 64) ? (m0 & (~0ull << b)) : 0ull;
+        const uint64_t a1 = (b <= 64) ? m1 : (m1 & (~0ull << (b - 64)));
+        if (a0 | a1) {
+            const double A = 0.5 * (a_lo + a_hi);
+            const double* g = a.G + (size_t)i * nr;
+            if (!bee && __popcll((long long)a0) + __popcll((long long)a1) == 1) {
+                // one source on the segment: zeta_s = 1, and zeta_d = 1 without e
+                const int j = a0 ? __ffsll((long long)a0) - 1 : 64 + __ffsll((long long)a1) - 1;
+                const double np = ph[j] - A * __ldg(g + j);                   // Eq. 13-14
+                if (np > 0.0) ph[j] = np;
+                else { ph[j] = 0.0; if (j < 64) m0 &= ~(1ull << j); else m1 &= ~(1ull << (j - 64)); }
             } else {
-                int i = (int)floor((real)a.eta * sqrt(real(2) * d));
-                i = min(max(i, 0), nr - 2);
-                while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
-                while (i > 0 && r[i] > d) --i;
-                i0 = i; ni = 2;
-                if (lane == 0) {
-                    const real ra = r[i], rb = r[i + 1];
-                    wrad[0] = (rb - d) / (rb - ra);
-                    wrad[1] = (d - ra) / (rb - ra);
+                const double* id2 = a.ID2 + (size_t)i * nr;
+                const double* gi = a.GI + (size_t)i * nr;
+                double Ftot = 0.0;                                // Eq. 11 at the segment midpoint
+                for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Ftot = fma(ph[j], __ldg(id2 + j), Ftot); }
+                for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Ftot = fma(ph[j], __ldg(id2 + j), Ftot); }
+                if (Ftot > 0.0) {
+                    const double inv_F = recip_nr(Ftot);
+                    double zd = 1.0;                              // Eq. 17
+                    if (bee) {
+                        const double ev = alpha_at<MODE>(a, bee, i + 1, ie);
+                        if (ev > 0.0) zd = fmin(2.0, Ftot * recip_nr(ev));
+                    }
+                    const double cf = A * zd * inv_F;             // zeta_s = F_j / Ftot (Eq. 16)
+                    for (uint64_t w = a0; w; w &= w - 1) {
+                        const int j = __ffsll((long long)w) - 1;
+                        const double np = ph[j] - cf * (__ldg(gi + j) * ph[j]);                  // Eq. 13-14
+                        if (np > 0.0) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
+                    }
+                    for (uint64_t w = a1; w; w &= w - 1) {
+                        const int j = 64 + __ffsll((long long)w) - 1;
+                        const double np = ph[j] - cf * (__ldg(gi + j) * ph[j]);
+                        if (np > 0.0) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
+                    }
                 }
             }
         }
-        __syncwarp();
-        const int total = (int)en * ni;
-        for (int p = lane; p < total; p += 32) {
-            const int ei = p / ni, j = p - ei * ni;
-            const uint32_t ent = __ldg(a.tent + eo + ei);
-            const int b = (int)(ent >> 16) * nr + i0 + j;
-            const real wk = (real)(ent & 0xffffu) * inv_m3 * wrad[j];
-            if (alpha != real(0)) bin_add<MODE>(bins_a + b, wk * alpha);
-            if (do_e) bin_add<MODE>(bins_e + b, wk * e);
-        }
-        __syncwarp();
+        a_hi = a_lo;
     }
-    if (eps != real(0)) {
-        // W_f,3 (App. A.3): two points r_i <= d < r_{i+1} keeping the sum and
-        // the flux at the target exact
-        int i;
-        real w0, w1;
-        if (d >= rlast) {
-            i = nr - 2; w0 = real(0); w1 = real(1);
-        } else {
-            i = (int)floor((real)a.eta * sqrt(real(2) * d));
-            i = min(max(i, 0), nr - 2);
-            while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
-            while (i > 0 && r[i] > d) --i;
-            if (i == 0) {
-                w0 = real(0); w1 = real(1);
-            } else {
-                const real ri = r[i], rj = r[i + 1];
-                const real ia = real(1) / (ri * ri), ib = real(1) / (rj * rj), it = real(1) / (d * d);
-                w1 = (ia - it) / (ia - ib);
-                w0 = real(1) - w1;
-            }
-        }
-        for (int p = lane; p < 2 * (int)en; p += 32) {
-            const int ei = p >> 1, k = p & 1;
-            const uint32_t ent = __ldg(a.tent + eo + ei);
-            const real wk = (real)(ent & 0xffffu) * inv_m3 * (k ? w1 : w0);
-            if (wk != real(0)) bin_add<MODE>(bins_eps + (int)(ent >> 16) * nr + i + k, wk * eps);
-        }
-        __syncwarp();
-    }
-}
-
-// Far-to-near sweep of one ray (Sec. 2.5): al = alpha per volume, ph = photon
-// rates per steradian (Phi_j, updated in place), ev = energy density or NULL.
-__device__ double sweep_ray(const WalkArgs& a, const double* al, double* ph, const double* ev) {
-    const int nr = a.nr;
-    uint64_t m0 = 0, m1 = 0;
-    for (int j = 1; j < nr; ++j)
-        if (ph[j] > 0.0) { if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64); }
-    if (!(m0 | m1)) return 0.0;
-    const int jtop = m1 ? 64 + 63 - __clzll((long long)m1) : 63 - __clzll((long long)m0);
-    for (int i = jtop - 1; i >= 0; --i) {
-        // sources strictly beyond r_i
-        const int b = i + 1;
-        uint64_t a0 = (b < 64) ? (m0 & (~0ull << b)) : 0ull;
-        uint64_t a1 = (b <= 64) ? m1 : (m1 & (~0ull << (b - 64)));
-        if (!(a0 | a1)) continue;
-        const double* id2 = a.ID2 + (size_t)i * nr;
-        const double* g = a.G + (size_t)i * nr;
-        double Ftot = 0.0;
-        for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Ftot += ph[j] * __ldg(id2 + j); }
-        for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Ftot += ph[j] * __ldg(id2 + j); }
-        if (!(Ftot > 0.0)) continue;
-        double zd = 1.0;                                       // Eq. 17
-        if (ev && ev[i + 1] > 0.0) zd = fmin(2.0, Ftot / ev[i + 1]);
-        const double A = 0.5 * (al[i] + al[i + 1]);
-        const double cf = A * zd / Ftot;                       // zeta_s = F_j / Ftot (Eq. 16)
-        for (uint64_t w = a0; w; w &= w - 1) {
-            const int j = __ffsll((long long)w) - 1;
-            const double R = cf * __ldg(g + j) * (ph[j] * __ldg(id2 + j));     // Eq. 14
-            const double np = ph[j] - R;                                      // Eq. 13
-            if (np > 0.0) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
-        }
-        for (uint64_t w = a1; w; w &= w - 1) {
-            const int j = 64 + __ffsll((long long)w) - 1;
-            const double R = cf * __ldg(g + j) * (ph[j] * __ldg(id2 + j));
-            const double np = ph[j] - R;
-            if (np > 0.0) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
-        }
-    }
-    double F0 = 0.0;                                            // Eq. 10-11 at r = 0
-    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; F0 += ph[j] * __ldg(a.inv_r2 + j); }
-    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; F0 += ph[j] * __ldg(a.inv_r2 + j); }
+    double F0 = 0.0;                                              // Eq. 10-11 at r = 0
+    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
+    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
     return F0;
 }
 
-// Convert the bins in place into FP64 per-volume coefficients and photon
-// rates, sweep all rays and return the warp's total flux (scaled units).
-template <int MODE>
-__device__ double sweep_bins(const WalkArgs& a, double* bins_a, double* bins_eps, double* bins_e, int lane) {
-    const int nr = a.nr, nbins = a.npix * nr;
-    for (int b = lane; b < nbins; b += 32) {
-        const int i = b % nr;
-        const double vol = __ldg(a.vol + i);
-        const double va = bin_value<MODE>(bins_a + b);
-        const double ve = bin_value<MODE>(bins_eps + b);
-        bins_a[b] = va / vol;
-        bins_eps[b] = ve / (4.0 * PI_D);                        // Eq. 12
-        if (a.use_e) bins_e[b] = bin_value<MODE>(bins_e + b) / vol;
+// The sweep of the FP32 form: the deposits (alpha, e) and the geometric
+// factors are FP32 quantities, so each segment's loss R_ij (Eq. 14) is formed
+// in FP32; the photon budget Phi_j from which the losses are subtracted, and
+// which cancels at the ionisation front, is kept and updated in FP64.
+__device__ __forceinline__ bool dpos(double v) { return __double_as_longlong(v) > 0; }   // v > 0
+
+template <>
+__device__ double sweep_ray<1>(const WalkArgs& a, const double* ba, double* be, const double* bee, const Scales& sc) {
+    const int nr = a.nr;
+    uint64_t m0 = 0, m1 = 0;
+    for (int j = 1; j < nr; ++j) {
+        if (bin_nonzero<1>(be + j)) {
+            if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64);
+        }
     }
-    __syncwarp();
-    double F = 0.0;
-    for (int k = lane; k < a.npix; k += 32)
-        F += sweep_ray(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr);
-    return warp_sum(F);
+    if (!(m0 | m1)) return 0.0;
+    const double inv4pi = 1.0 / (4.0 * PI_D);
+    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; be[j] = bin_value<1>(be + j, sc.eps) * inv4pi; }
+    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; be[j] = bin_value<1>(be + j, sc.eps) * inv4pi; }
+    double* ph = be;                                              // Eq. 12
+    const float ia = 1.0f / sc.a, ie = 1.0f / sc.e;
+    const int jtop = m1 ? 64 + 63 - __clzll((long long)m1) : 63 - __clzll((long long)m0);
+    float a_hi = bin_value_f<1>(ba + jtop, ia) * __ldg(a.inv_volf + jtop);
+    for (int i = jtop - 1; i >= 0 && (m0 | m1); --i) {
+        const float a_lo = bin_value_f<1>(ba + i, ia) * __ldg(a.inv_volf + i);
+        const int b = i + 1;
+        const uint64_t a0 = (b < 64) ? (m0 & (~0ull << b)) : 0ull;
+        const uint64_t a1 = (b <= 64) ? m1 : (m1 & (~0ull << (b - 64)));
+        if (a0 | a1) {
+            const float A = 0.5f * (a_lo + a_hi);
+            if (!bee && __popcll((long long)a0) + __popcll((long long)a1) == 1) {
+                const int j = a0 ? __ffsll((long long)a0) - 1 : 64 + __ffsll((long long)a1) - 1;
+                const double np = ph[j] - (double)(A * __ldg(a.Gf + (size_t)i * nr + j));      // Eq. 13-14
+                if (dpos(np)) ph[j] = np;
+                else { ph[j] = 0.0; if (j < 64) m0 &= ~(1ull << j); else m1 &= ~(1ull << (j - 64)); }
+            } else {
+                const float* id2 = a.ID2f + (size_t)i * nr;
+                const float* gi = a.GIf + (size_t)i * nr;
+                float Ftot = 0.f;                                 // Eq. 11 at the segment midpoint
+                for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Ftot = fmaf((float)ph[j], __ldg(id2 + j), Ftot); }
+                for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Ftot = fmaf((float)ph[j], __ldg(id2 + j), Ftot); }
+                if (Ftot > 0.f) {
+                    float zd = 1.f;                               // Eq. 17
+                    if (bee) {
+                        const float ev = bin_value_f<1>(bee + i + 1, ie) * __ldg(a.inv_volf + i + 1);
+                        if (ev > 0.f) zd = fminf(2.f, Ftot / ev);
+                    }
+                    const float cf = A * zd / Ftot;               // zeta_s = F_j / Ftot (Eq. 16)
+                    for (uint64_t w = a0; w; w &= w - 1) {
+                        const int j = __ffsll((long long)w) - 1;
+                        const double np = ph[j] - (double)(cf * (__ldg(gi + j) * (float)ph[j]));   // Eq. 13-14
+                        if (dpos(np)) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
+                    }
+                    for (uint64_t w = a1; w; w &= w - 1) {
+                        const int j = 64 + __ffsll((long long)w) - 1;
+                        const double np = ph[j] - (double)(cf * (__ldg(gi + j) * (float)ph[j]));
+                        if (dpos(np)) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
+                    }
+                }
+            }
+        }
+        a_hi = a_lo;
+    }
+    double F0 = 0.0;                                              // Eq. 10-11 at r = 0
+    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
+    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
+    return F0;
 }
 
-template <int MODE, bool DUMP>
-__global__ void __launch_bounds__(32) k_walk(WalkArgs a) {
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t += red[w];
+    return t;                                                      // valid in thread 0
+}
+
+// One CTA of NT threads per target (persistent over targets).  Each step
+// pops NT/8 opened nodes and evaluates their NT children, one per thread.
+template <int MODE, bool DUMP, int NT>
+__global__ void __launch_bounds__(NT) k_walk(WalkArgs a) {
     using real = typename Prec<MODE>::real;
+    constexpr int NW = NT / 32, P = NT / 8;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x;
+    __shared__ int s_wcnt[NW], s_bcnt[NW], s_pcnt[NW];
+    __shared__ double s_red[NW];
+    __shared__ unsigned int s_q;
+    __shared__ int s_nacc;
+    __shared__ RadialSpread<MODE> s_node[NT];                    // the step's nodes to spread
+    __shared__ int s_pair0[NT + 1];                              // their first (node, ray) pair
+    __shared__ real s_w[NT * MAXW];                              // W_p values kept by the setup threads
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nr = a.nr, nbins = a.npix * nr;
     const int nq = a.use_e ? 3 : 2;
     double* bins_a = reinterpret_cast<double*>(smem);
     double* bins_eps = bins_a + nbins;
     double* bins_e = a.use_e ? bins_eps + nbins : nullptr;
     uint32_t* stack = reinterpret_cast<uint32_t*>(bins_a + (size_t)nq * nbins);
-    real* wrad = reinterpret_cast<real*>(stack + a.stack_cap);
     const int N = a.N, L = a.L;
     const unsigned lanemask_lt = (1u << lane) - 1u;
+    const real* rr = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
+    const real inv_m3 = real(1.0) / real(TM * TM * TM);
+    unsigned long long n_vis = 0, n_acc = 0, n_ent = 0;      // per-thread counters
+    Scales sc{1.f, 1.f, 1.f};
+    if (MODE == 1) {                                         // fixed-point units from the root totals
+        real cm0[3], m0, q0[3], mi0;
+        load_node<MODE>(a.nodes, 0, cm0, m0, q0, mi0);
+        sc.a = fixed_scale((float)q0[0]);
+        sc.eps = fixed_scale((float)q0[1]);
+        sc.e = fixed_scale((float)q0[2]);
+    }
 
     for (;;) {
-        unsigned int qq = 0;
-        if (lane == 0) qq = atomicAdd(a.counter, 1u);
-        const int64_t q = (int64_t)__shfl_sync(FULL, qq, 0);
+        if (tid == 0) s_q = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int64_t q = (int64_t)s_q;
         if (q >= a.n_targets) break;
         int tx, ty, tz;
         int64_t cell;
@@ -362,25 +531,27 @@ __global__ void __launch_bounds__(32) k_walk(WalkArgs a) {
             cell = ((int64_t)tz * N + ty) * N + tx;
         }
         const real px = (real)tx + real(0.5), py = (real)ty + real(0.5), pz = (real)tz + real(0.5);
-        for (int b = lane; b < nq * nbins; b += 32) bins_a[b] = 0.0;
-        if (lane == 0) stack[0] = 0u;                           // the root, opened
-        int top = 1, nacc = 0;
+        for (int b = tid; b < nq * nbins; b += NT) bins_a[b] = 0.0;
+        if (tid == 0) { stack[0] = 0u; s_nacc = 0; }               // the root, opened
+        int top = 1, max_top = 1;
         bool overflow = false;
-        __syncwarp();
+        __syncthreads();
         while (top > 0) {
-            const int np = min(4, top);
-            const int pi = lane >> 3, c = lane & 7;
+            const int np = min(P, top);
+            const int pi = tid >> 3, c = tid & 7;
             const uint32_t pe = (pi < np) ? stack[top - np + pi] : 0u;
-            __syncwarp();
+            __syncthreads();                                     // parents read before the pushes
             top -= np;
-            int action = 0;                                     // 1 open, 2 accept
-            int lev = 0, s = 0, key = 0;
+            int action = 0;                                      // 1 open, 2 accept
+            int lev = 0, ne = 0;
             uint32_t mort = 0;
-            real d = real(0), alpha = real(0), eps = real(0), e = real(0);
+            RadialSpread<MODE> node;
+            bool spread = false;
             if (pi < np) {
+                ++n_vis;
                 lev = (int)(pe >> 27) + 1;
                 mort = ((pe & 0x7ffffffu) << 3) | (uint32_t)c;
-                s = N >> lev;
+                const int s = N >> lev;
                 const int cx = (int)compact3(mort) * s, cy = (int)compact3(mort >> 1) * s,
                           cz = (int)compact3(mort >> 2) * s;
                 const bool contains = (tx >= cx && tx < cx + s) && (ty >= cy && ty < cy + s) &&
@@ -396,96 +567,179 @@ __global__ void __launch_bounds__(32) k_walk(WalkArgs a) {
                         action = 1;
                     } else {
                         action = 2;
-                        d = sqrt(d2);
-                        alpha = qv[0]; eps = qv[1]; e = qv[2];
-                        key = table_key(2 * cx + s - 2 * tx - 1, 2 * cy + s - 2 * ty - 1, 2 * cz + s - 2 * tz - 1, s);
+                        const real d = sqrt(d2);
+                        const bool in_reach = (MODE == 0) ? ((double)d <= a.lray) : ((float)d <= a.lrayf);
+                        const bool has_ae = qv[0] != real(0) || (a.use_e && qv[2] != real(0));
+                        if (in_reach && (has_ae || qv[1] != real(0))) {
+                            const int key = table_key(2 * cx + s - 2 * tx - 1, 2 * cy + s - 2 * ty - 1,
+                                                      2 * cz + s - 2 * tz - 1, s);
+                            const uint2 hd = __ldg(a.hdr + key);
+                            ne = (int)hd.y;
+                            n_ent += ne;
+                            if (qv[1] != real(0)) deposit_eps<MODE>(a, bins_eps, hd.x, ne, d, qv[1], sc.eps);
+                            if (has_ae && ne > 0) {
+                                radial_setup<MODE>(a, node, d, s, s_w + tid * MAXW);
+                                node.src = (uint16_t)tid;
+                                node.alpha = qv[0];
+                                node.e = a.use_e ? qv[2] : real(0);
+                                node.off = hd.x;
+                                spread = true;
+                            }
+                        }
                     }
                 }
             }
-            const unsigned open_mask = __ballot_sync(FULL, action == 1);
-            const int nopen = __popc(open_mask);
-            if (top + nopen > a.stack_cap) { overflow = true; break; }
-            if (action == 1) stack[top + __popc(open_mask & lanemask_lt)] = ((uint32_t)lev << 27) | mort;
-            top += nopen;
-            unsigned acc_mask = __ballot_sync(FULL, action == 2);
-            if (DUMP) {
-                if (action == 2) {
-                    const int slot = nacc + __popc(acc_mask & lanemask_lt);
+            // block-wide offsets of the pushes and of the nodes to spread
+            const unsigned om = __ballot_sync(FULL, action == 1);
+            const unsigned bm = __ballot_sync(FULL, spread);
+            int pc = spread ? ne : 0;                             // (node, ray) pairs of this thread
+            int incl = pc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) s_pcnt[wid] = incl;
+            if (lane == 0) { s_wcnt[wid] = __popc(om); s_bcnt[wid] = __popc(bm); }
+            __syncthreads();                                     // per-warp counts visible
+            int obase = 0, ototal = 0, nbase = 0, ntotal = 0, pbase = 0, ptotal = 0;
+            for (int w = 0; w < NW; ++w) {
+                const int oc = s_wcnt[w], bc = s_bcnt[w], pcw = s_pcnt[w];
+                if (w < wid) { obase += oc; nbase += bc; pbase += pcw; }
+                ototal += oc; ntotal += bc; ptotal += pcw;
+            }
+            if (top + ototal > a.stack_cap) overflow = true;     // same value in every thread
+            if (!overflow) {
+                if (action == 1) stack[top + obase + __popc(om & lanemask_lt)] = ((uint32_t)lev << 27) | mort;
+                if (spread) {
+                    const int k = nbase + __popc(bm & lanemask_lt);
+                    s_node[k] = node;
+                    s_pair0[k] = pbase + incl - pc;
+                }
+                if (tid == 0) s_pair0[ntotal] = ptotal;
+            }
+            if (action == 2) {
+                ++n_acc;
+                if (DUMP) {
+                    const int slot = atomicAdd(&s_nacc, 1);
                     if (slot < a.acc_cap) a.ids_out[q * a.acc_cap + slot] = (int32_t)(level_offset(lev) + mort);
                 }
-                nacc += __popc(acc_mask);
             }
-            while (acc_mask) {
-                const int src = __ffs(acc_mask) - 1;
-                acc_mask &= acc_mask - 1;
-                const real al_b = __shfl_sync(FULL, alpha, src), ep_b = __shfl_sync(FULL, eps, src);
-                const real e_b = __shfl_sync(FULL, e, src);
-                const real d_b = __shfl_sync(FULL, d, src);
-                const int s_b = __shfl_sync(FULL, s, src), key_b = __shfl_sync(FULL, key, src);
-                const bool in_reach = (MODE == 0) ? ((double)d_b <= a.lray) : ((float)d_b <= a.lrayf);
-                if (in_reach && (al_b != real(0) || ep_b != real(0) || (a.use_e && e_b != real(0))))
-                    map_node<MODE>(a, bins_a, bins_eps, bins_e, wrad, key_b, d_b, s_b, al_b, ep_b, e_b, lane);
+            __syncthreads();                                     // pushes and spread list visible
+            if (overflow) break;
+            // spread the step's nodes: each thread takes a contiguous run of
+            // (node, table entry) pairs
+            if (ptotal > 0) {
+                const int chunk = (ptotal + NT - 1) / NT;
+                const int p0 = tid * chunk, p1 = min(p0 + chunk, ptotal);
+                if (p0 < p1) {
+                    int k = 0, hi = ntotal - 1;
+                    while (k < hi) {
+                        const int mid = (k + hi + 1) >> 1;
+                        if (s_pair0[mid] <= p0) k = mid; else hi = mid - 1;
+                    }
+                    RadialSpread<MODE> n = s_node[k];
+                    int kend = s_pair0[k + 1];
+                    for (int p = p0; p < p1; ++p) {
+                        if (p >= kend) { ++k; n = s_node[k]; kend = s_pair0[k + 1]; }
+                        const uint32_t en = __ldg(a.tent + n.off + (p - s_pair0[k]));
+                        const int b0 = (int)(en >> 16) * nr + n.lo;
+                        const real wk = (real)(en & 0xffffu) * inv_m3;
+                        for (int j = 0; j < n.npts; ++j) {
+                            const real w = spread_weight<MODE>(n, j, rr, s_w) * wk;
+                            if (w == real(0)) continue;
+                            if (n.alpha != real(0)) bin_atomic_add<MODE>(bins_a + b0 + j, w * n.alpha, sc.a);
+                            if (a.use_e && n.e != real(0)) bin_atomic_add<MODE>(bins_e + b0 + j, w * n.e, sc.e);
+                        }
+                    }
+                }
             }
-            __syncwarp();
+            top += ototal;
+            max_top = max(max_top, top);
         }
+        __syncthreads();                                         // all spreads done
         // own emission of the target (Sec. 2.5 footnote: target sphere r_tp = dx/2)
         real cmt[3], mt, qt[3], miont;
         load_node<MODE>(a.nodes, level_offset(L) + morton3(tx, ty, tz), cmt, mt, qt, miont);
         const double eps_self = (double)qt[1];
+        if (tid == 0) atomicMax(a.status + 1, max_top);
         if (overflow) {
-            if (lane == 0) {
+            if (tid == 0) {
                 atomicAdd(a.status, 1);
                 if (a.F) a.F[a.targets ? q : cell] = __longlong_as_double(0x7ff8000000000000LL);
             }
             continue;
         }
-        if (DUMP) {
+        if (DUMP) {                                              // raw bins, as the sweep reads them
             double* out = a.bins_out + (size_t)q * 3 * nbins;
-            for (int b = lane; b < nbins; b += 32) {
-                out[b] = bin_value<MODE>(bins_a + b);
-                out[nbins + b] = bin_value<MODE>(bins_eps + b);
-                out[2 * nbins + b] = a.use_e ? bin_value<MODE>(bins_e + b) : 0.0;
+            for (int b = tid; b < nbins; b += NT) {
+                out[b] = bins_a[b];
+                out[nbins + b] = bins_eps[b];
+                out[2 * nbins + b] = a.use_e ? bins_e[b] : 0.0;
             }
-            if (lane == 0) { a.counts_out[q] = nacc; a.eps_self_out[q] = eps_self; }
-            __syncwarp();
+            if (tid == 0) {
+                a.counts_out[q] = s_nacc;
+                a.eps_self_out[q] = eps_self;
+                if (q == 0) { a.scales_out[0] = sc.a; a.scales_out[1] = sc.eps; a.scales_out[2] = sc.e; }
+            }
             continue;
         }
-        const double F = sweep_bins<MODE>(a, bins_a, bins_eps, bins_e, lane) + eps_self / (4.0 * PI_D * 0.25);
-        if (lane == 0) {
+        double Fk = 0.0;
+        for (int k = tid; k < a.npix; k += NT)
+            Fk += sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
+        const double F = block_sum<NT>(Fk, s_red) + eps_self / (4.0 * PI_D * 0.25);
+        if (tid == 0) {
             const int64_t o = a.targets ? q : cell;
             if (a.F) a.F[o] = F * a.Fconv;
             if (a.E) a.E[o] = F * a.Econv;
             if (a.ion) a.ion[o] = (uint8_t)(F > 0.0);
         }
-        __syncwarp();
+    }
+    // kernel-wide counters, one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        n_vis += __shfl_xor_sync(FULL, n_vis, o);
+        n_acc += __shfl_xor_sync(FULL, n_acc, o);
+        n_ent += __shfl_xor_sync(FULL, n_ent, o);
+    }
+    if (lane == 0) {
+        atomicAdd(a.stats + 0, n_vis);
+        atomicAdd(a.stats + 1, n_acc);
+        atomicAdd(a.stats + 2, n_ent);
     }
 }
 
-// Unfused sweep over bins stored by the dump walk: one warp per target.
-__global__ void __launch_bounds__(32) k_sweep_stored(WalkArgs a, const double* bins_in, const double* eps_self) {
+// Unfused sweep over bins stored by the dump walk: one CTA per target.
+template <int MODE, int NT>
+__global__ void __launch_bounds__(NT) k_sweep_stored(WalkArgs a, const double* bins_in, const double* eps_self) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x;
+    __shared__ double s_red[NT / 32];
+    const int tid = threadIdx.x;
     const int nbins = a.npix * a.nr;
     double* bins_a = reinterpret_cast<double*>(smem);
     double* bins_eps = bins_a + nbins;
     double* bins_e = a.use_e ? bins_eps + nbins : nullptr;
     for (int64_t q = blockIdx.x; q < a.n_targets; q += gridDim.x) {
         const double* in = bins_in + (size_t)q * 3 * nbins;
-        for (int b = lane; b < nbins; b += 32) {
+        __syncthreads();
+        for (int b = tid; b < nbins; b += NT) {
             bins_a[b] = in[b];
             bins_eps[b] = in[nbins + b];
             if (a.use_e) bins_e[b] = in[2 * nbins + b];
         }
-        __syncwarp();
-        const double F = sweep_bins<0>(a, bins_a, bins_eps, bins_e, lane) + eps_self[q] / (4.0 * PI_D * 0.25);
-        if (lane == 0) {
+        __syncthreads();
+        double Fk = 0.0;
+        for (int k = tid; k < a.npix; k += NT)
+            Fk += sweep_ray<MODE>(a, bins_a + k * a.nr, bins_eps + k * a.nr, a.use_e ? bins_e + k * a.nr : nullptr,
+                                  Scales{a.scales_in[0], a.scales_in[1], a.scales_in[2]});
+        const double F = block_sum<NT>(Fk, s_red) + eps_self[q] / (4.0 * PI_D * 0.25);
+        if (tid == 0) {
             if (a.F) a.F[q] = F * a.Fconv;
             if (a.E) a.E[q] = F * a.Econv;
             if (a.ion) a.ion[q] = (uint8_t)(F > 0.0);
         }
-        __syncwarp();
     }
 }
+
+constexpr int WALK_NT = 128;                // threads per target (one CTA)
 
 WalkArgs make_args(const tr_tree* t) {
     WalkArgs a{};
@@ -498,24 +752,24 @@ WalkArgs make_args(const tr_tree* t) {
     a.lray = t->lray;
     a.th_lim2f = (float)a.th_lim2; a.th_if2f = (float)a.th_if2; a.th_src2f = (float)a.th_src2;
     a.lrayf = (float)t->lray;
-    a.toff = t->table->off; a.tent = t->table->ent;
-    a.r = t->sw.r; a.rf = t->sw.rf; a.inv_r2 = t->sw.inv_r2; a.vol = t->sw.vol; a.G = t->sw.G; a.ID2 = t->sw.ID2;
+    a.toff = t->table->off; a.tent = t->table->ent; a.hdr = t->table->hdr;
+    a.r = t->sw.r; a.rf = t->sw.rf; a.inv_r2 = t->sw.inv_r2; a.inv_vol = t->sw.inv_vol; a.inv_volf = t->sw.inv_volf; a.G = t->sw.G; a.ID2 = t->sw.ID2; a.GI = t->sw.GI; a.Gf = t->sw.Gf; a.ID2f = t->sw.ID2f; a.GIf = t->sw.GIf;
     a.Fconv = t->U / (t->dx * t->dx);
     a.Econv = t->Eu;
     a.status = t->status;
+    a.stats = t->stats;
     a.counter = t->counter;
     return a;
 }
 
-int stack_cap_for(const tr_tree* t) {
-    // opened nodes pending on the stack stay well below this for theta >= 0.25
-    (void)t;
-    return 2048;
-}
+// Opened nodes waiting on a target's stack.  The stack never holds more
+// than the target's opened nodes (a few hundred at theta = 0.5); overflow
+// is detected and reported, never written past.
+constexpr int STACK_CAP = 512;
 
-size_t walk_smem(const tr_tree* t, int stack_cap) {
+size_t walk_smem(const tr_tree* t) {
     const int nq = t->use_e ? 3 : 2;
-    return (size_t)nq * t->npix * t->nr * 8 + (size_t)stack_cap * 4 + MAX_NR * 8;
+    return (size_t)nq * t->npix * t->nr * 8 + (size_t)STACK_CAP * 4;
 }
 
 template <typename K>
@@ -526,12 +780,14 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs& a, cudaStream
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, smem), "occupancy query");
+    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WALK_NT, smem), "occupancy query");
     if (s != TR_OK) return s;
-    if (per_sm < 1) return set_error(TR_EUNSUPPORTED, "ray bins need %zu bytes of shared memory per warp", smem);
+    if (per_sm < 1) return set_error(TR_EUNSUPPORTED, "ray bins need %zu bytes of shared memory per target", smem);
     s = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st), "counter reset");
     if (s != TR_OK) return s;
-    kernel<<<sms * per_sm, 32, smem, st>>>(a);
+    int64_t blocks = (int64_t)sms * per_sm;
+    if (blocks > a.n_targets) blocks = a.n_targets > 0 ? a.n_targets : 1;
+    kernel<<<(unsigned)blocks, WALK_NT, smem, st>>>(a);
     return cuda_check(cudaGetLastError(), "walk kernel launch");
 }
 
@@ -544,33 +800,39 @@ tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, 
     a.n_targets = n_targets;
     a.F = out.F; a.E = out.e; a.ion = out.ion;
     a.bins_out = out.bins; a.ids_out = out.ids; a.counts_out = out.counts; a.eps_self_out = out.eps_self;
+    a.scales_out = out.scales;
     a.acc_cap = out.acc_cap;
-    a.stack_cap = stack_cap_for(t);
-    const size_t smem = walk_smem(t, a.stack_cap);
+    a.stack_cap = STACK_CAP;
+    const size_t smem = walk_smem(t);
     tr_status s = cuda_check(cudaMemsetAsync(t->status, 0, 4 * sizeof(int32_t), st), "status reset");
+    if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
     if (s != TR_OK) return s;
-    if (t->mode == 0) s = dump ? launch_persistent(k_walk<0, true>, smem, a, st) : launch_persistent(k_walk<0, false>, smem, a, st);
-    else s = dump ? launch_persistent(k_walk<1, true>, smem, a, st) : launch_persistent(k_walk<1, false>, smem, a, st);
+    if (t->mode == 0)
+        s = dump ? launch_persistent(k_walk<0, true, WALK_NT>, smem, a, st) : launch_persistent(k_walk<0, false, WALK_NT>, smem, a, st);
+    else
+        s = dump ? launch_persistent(k_walk<1, true, WALK_NT>, smem, a, st) : launch_persistent(k_walk<1, false, WALK_NT>, smem, a, st);
     return s;
 }
 
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st) {
     WalkArgs a{};
     a.nr = r->nr; a.npix = r->npix; a.use_e = r->use_e;
-    a.r = r->sw.r; a.inv_r2 = r->sw.inv_r2; a.vol = r->sw.vol; a.G = r->sw.G; a.ID2 = r->sw.ID2;
+    a.r = r->sw.r; a.inv_r2 = r->sw.inv_r2; a.inv_vol = r->sw.inv_vol; a.inv_volf = r->sw.inv_volf; a.G = r->sw.G; a.ID2 = r->sw.ID2; a.GI = r->sw.GI; a.Gf = r->sw.Gf; a.ID2f = r->sw.ID2f; a.GIf = r->sw.GIf;
     a.n_targets = r->n_targets;
     a.Fconv = r->U / (r->dx * r->dx);
     a.Econv = r->Eu;
     a.F = F; a.E = e; a.ion = ion;
+    a.scales_in = r->scales;
     const size_t smem = (size_t)(r->use_e ? 3 : 2) * r->npix * r->nr * 8;
-    tr_status s = cuda_check(cudaFuncSetAttribute(k_sweep_stored, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+    auto kern = r->mode == 0 ? k_sweep_stored<0, WALK_NT> : k_sweep_stored<1, WALK_NT>;
+    tr_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "cudaFuncSetAttribute(sweep smem)");
     if (s != TR_OK) return s;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t blocks = r->n_targets < (int64_t)sms * 8 ? r->n_targets : (int64_t)sms * 8;
-    if (blocks > 0) k_sweep_stored<<<(unsigned)blocks, 32, smem, st>>>(a, r->bins, r->eps_self);
+    const int64_t blocks = r->n_targets < (int64_t)sms * 4 ? r->n_targets : (int64_t)sms * 4;
+    if (blocks > 0) kern<<<(unsigned)blocks, WALK_NT, smem, st>>>(a, r->bins, r->eps_self);
     return cuda_check(cudaGetLastError(), "sweep kernel launch");
 }
 
