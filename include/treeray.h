@@ -143,6 +143,29 @@ tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p,
                    double* F_out, double* e_out, uint8_t* ion_out,
                    int32_t* iters_out, double* delta_out, tr_stream stream);
 
+/* One pass of tr_solve (build + walk + map + sweep, max_iter = 1) that
+ * allocates no device memory.  The paper has no counterpart: this is a
+ * service to callers that cannot call cudaMalloc, such as code that runs
+ * while a CUDA graph is being captured (an allocation would break or
+ * escape the capture), applications whose device memory is owned by a pool
+ * or arena that forbids outside allocations, and real-time or embedded hosts
+ * that must not allocate once running.  The caller still supplies inputs and
+ * outputs (as for tr_solve: N^3 device arrays, NULL allowed).
+ * Working memory is one fixed device array (about 16 MB) inside the library,
+ * held by every GPU that loads it until the process exits.  Limits: N <= 32,
+ * N_side 1 or 2, N_R <= 128, max_iter = 1; larger requests return
+ * TR_EUNSUPPORTED with a message and touch nothing.
+ * The first call on a device looks up that array's device address and
+ * builds the node->ray table into it, synchronising `stream`; make that
+ * first call (and the first call with a new N_side) before any stream
+ * capture.  All calls share the array and it keeps the last call's
+ * contents; every value a pass needs is rewritten or cleared by that pass.
+ * Calls whose GPU work overlaps (e.g. two streams driven from two host
+ * threads that bypass its host lock) race on the array.  Synchronises
+ * `stream`.  Errors: TR_EINVAL, TR_EUNSUPPORTED, TR_ECUDA, TR_EOVERFLOW. */
+tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, const tr_params* p,
+                           double* F_out, double* e_out, uint8_t* ion_out, tr_stream stream);
+
 /* ---- inspection (parity tests) -------------------------------------- */
 
 /* Sizes of a tree: node count, levels (log2 N + 1), N_R, N_PIX. Host outputs. */

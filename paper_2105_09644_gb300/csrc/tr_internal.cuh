@@ -121,6 +121,10 @@ tr_status cuda_check(cudaError_t e, const char* what);
 
 // table (tr_table.cu)
 tr_status table_get(int nside, const Table** out, cudaStream_t st);
+// build the table into caller-provided device memory (t->off, t->ent, t->hdr
+// set; counts: NKEYS words of scratch); TR_EUNSUPPORTED if it needs more
+// than ent_capacity entries.  Synchronises st.
+tr_status table_build_into(int nside, Table* t, uint32_t* counts, uint32_t ent_capacity, cudaStream_t st);
 
 // tree (tr_tree.cu)
 tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStream_t st);
@@ -128,6 +132,8 @@ tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st);
 tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g,
                             cudaStream_t st);
 void sweep_tables_free(SweepTables* sw);
+// fill tables whose device pointers are already set (no allocation)
+tr_status sweep_tables_fill(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g, cudaStream_t st);
 
 // walk (tr_walk.cu)
 struct WalkOut {

@@ -206,4 +206,26 @@ tr_status table_get(int nside, const Table** out, cudaStream_t st) {
     return TR_OK;
 }
 
+tr_status table_build_into(int nside, Table* t, uint32_t* counts, uint32_t ent_capacity, cudaStream_t st) {
+    const int npix = 12 * nside * nside;
+    const size_t shm = sizeof(int) * (size_t)npix;
+    k_table_count<<<NKEYS, 256, shm, st>>>(nside, counts);
+    k_scan<<<1, 1024, 0, st>>>(counts, t->off, NKEYS);
+    uint32_t total = 0;
+    tr_status s = cuda_check(cudaMemcpyAsync(&total, t->off + NKEYS, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                             "table size copy");
+    if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "table count kernels");
+    if (s != TR_OK) return s;
+    if (total > ent_capacity)
+        return set_error(TR_EUNSUPPORTED, "node->ray table for N_side %d needs %u entries, room for %u", nside, total,
+                         ent_capacity);
+    k_table_fill<<<NKEYS, 256, shm, st>>>(nside, t->off, t->ent);
+    k_table_hdr<<<(NKEYS + 255) / 256, 256, 0, st>>>(t->off, t->hdr, NKEYS);
+    s = cuda_check(cudaStreamSynchronize(st), "table fill kernels");
+    if (s != TR_OK) return s;
+    t->nside = nside;
+    t->n_entries = (int)total;
+    return TR_OK;
+}
+
 }  // namespace tr

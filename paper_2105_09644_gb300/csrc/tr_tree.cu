@@ -230,6 +230,17 @@ tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npi
     return TR_OK;
 }
 
+tr_status sweep_tables_fill(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g, cudaStream_t st) {
+    const size_t n2 = (size_t)nr * nr;
+    k_sweep_tables<<<grid_for((int64_t)n2, 128), 128, 0, st>>>(nr, eta, nside, npix, zeta_g, sw->r, sw->rf,
+                                                                sw->inv_r2, sw->inv_vol, sw->inv_volf, sw->G, sw->ID2,
+                                                                sw->GI, sw->Gf, sw->ID2f, sw->GIf);
+    tr_status s = cuda_check(cudaGetLastError(), "ray table kernel");
+    if (s != TR_OK) return s;
+    sw->nr = nr; sw->eta = eta; sw->nside = nside; sw->zeta_g = zeta_g;
+    return TR_OK;
+}
+
 void sweep_tables_free(SweepTables* sw) {
     cudaFree(sw->r); cudaFree(sw->rf); cudaFree(sw->inv_r2); cudaFree(sw->inv_vol); cudaFree(sw->inv_volf);
     cudaFree(sw->G); cudaFree(sw->ID2); cudaFree(sw->GI); cudaFree(sw->Gf); cudaFree(sw->ID2f); cudaFree(sw->GIf);
