@@ -143,6 +143,16 @@ tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p,
                    double* F_out, double* e_out, uint8_t* ion_out,
                    int32_t* iters_out, double* delta_out, tr_stream stream);
 
+/* Fractional change of the energy density between two passes (Sec. 2.6):
+ * delta_mode 0: delta_cell = max_c |e_new - e_old| / max(e_old, e_med)
+ * (Eq. 21, e_med the lower median of e_old, absolute difference); 1:
+ * delta_tot = 2 |sum e_new - sum e_old| / (sum e_new + sum e_old) (Eq. 20).
+ * e_new, e_old: device arrays of n >= 1 values (erg cm^-3, >= 0).
+ * *delta_out (HOST) receives delta; a zero norm with a change gives
+ * INFINITY.  Synchronises `stream`.  Errors: TR_EINVAL, TR_ENOMEM, TR_ECUDA. */
+tr_status tr_delta(const double* e_new, const double* e_old, int64_t n, int32_t delta_mode,
+                   double* delta_out, tr_stream stream);
+
 /* One pass of tr_solve (build + walk + map + sweep, max_iter = 1) that
  * allocates no device memory.  The paper has no counterpart: this is a
  * service to callers that cannot call cudaMalloc, such as code that runs

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_EINVAL", 2: "TR_ENOMEM", 3: "TR_ECUDA", 4: "T
 
 # every symbol include/treeray.h declares
 EXPORTED = ["tr_params_default", "tr_build_tree", "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve",
-            "tr_tree_stats", "tr_solve_noalloc",
+            "tr_tree_stats", "tr_solve_noalloc", "tr_delta",
             "tr_tree_info", "tr_tree_nodes", "tr_rays_info", "tr_rays_export", "tr_table_info",
             "tr_table_export", "tr_tree_free", "tr_rays_free", "tr_last_error"]
 
@@ -69,6 +69,7 @@ def load():
     L.tr_ray_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_walk_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_tree_stats.argtypes = [vp, C.POINTER(i64)]
+    L.tr_delta.argtypes = [vp, vp, i64, i32, C.POINTER(C.c_double), vp]
     L.tr_solve_noalloc.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), vp, vp, vp, vp]
     L.tr_solve.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), vp, vp, vp,
                            C.POINTER(i32), C.POINTER(C.c_double), vp]
@@ -203,6 +204,12 @@ def tr_solve(grid: Grid, sources: Sources, params: Params, F=None, e=None, ion=N
     check(load().tr_solve(C.byref(grid), C.byref(sources), C.byref(params), _ptr(F), _ptr(e), _ptr(ion),
                           C.byref(iters), C.byref(delta), _stream(stream)))
     return iters.value, delta.value
+
+
+def tr_delta(e_new, e_old, mode: int = 0, stream=None) -> float:
+    out = C.c_double()
+    check(load().tr_delta(_ptr(e_new), _ptr(e_old), int(e_new.numel()), mode, C.byref(out), _stream(stream)))
+    return out.value
 
 
 def tr_solve_noalloc(grid: Grid, sources: Sources, params: Params, F=None, e=None, ion=None, stream=None):

@@ -84,6 +84,8 @@ void tree_release(tr_tree* t) {
     cudaFree(t->status);
     cudaFree(t->stats);
     cudaFree(t->counter);
+    cudaFree(t->e_work);
+    cudaFree(t->dscratch);
     sweep_tables_free(&t->sw);
     delete t;
 }
@@ -108,6 +110,7 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
     const size_t sum_bytes = (size_t)n_nodes * 3 * (mode == 0 ? sizeof(double) : sizeof(float));
     tr_tree* t = *inout;
     if (t && (t->N != N || t->mode != mode || t->device != dev)) {
+        // the iteration buffers belong to the tree and go with it
         tree_release(t);
         t = nullptr;
         *inout = nullptr;
@@ -294,21 +297,73 @@ tr_status tr_solve(const tr_grid* g, const tr_sources* s, const tr_params* p, do
     g_err[0] = '\0';
     cudaStream_t st = (cudaStream_t)stream;
     tr_status rc = check_params(p);
+    if (rc == TR_OK) rc = check_grid(g, s);
     if (rc != TR_OK) return rc;
-    if (p->max_iter > 1) return set_error(TR_EUNSUPPORTED, "max_iter > 1 is not available in this build");
+    if (!(p->eps_lim >= 0.0)) return set_error(TR_EINVAL, "eps_lim must be >= 0");
     int dev = 0;
     if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice")) != TR_OK) return rc;
     std::lock_guard<std::mutex> lock(g_solve_mu);
     tr_tree*& t = g_solve_trees[dev];
-    if ((rc = build(g, s, p, &t, st)) != TR_OK) return rc;
-    WalkOut o;
-    o.F = F_out; o.e = e_out; o.ion = ion_out;
-    const int64_t ncell = (int64_t)t->N * t->N * t->N;
-    if ((rc = walk_run(t, nullptr, ncell, false, o, st)) != TR_OK) return rc;
-    if ((rc = read_status(t, st)) != TR_OK) return rc;
-    if (iters_out) *iters_out = 1;
-    if (delta_out) *delta_out = INFINITY;
+    const int64_t ncell = (int64_t)g->N * g->N * g->N;
+    const bool need_delta = p->max_iter > 1 || (delta_out && g->e_prev);
+    if (!need_delta) {
+        // one pass (Sec. 2.3-2.5)
+        if ((rc = build(g, s, p, &t, st)) != TR_OK) return rc;
+        WalkOut o;
+        o.F = F_out; o.e = e_out; o.ion = ion_out;
+        if ((rc = walk_run(t, nullptr, ncell, false, o, st)) != TR_OK) return rc;
+        if ((rc = read_status(t, st)) != TR_OK) return rc;
+        if (iters_out) *iters_out = 1;
+        if (delta_out) *delta_out = INFINITY;
+        return TR_OK;
+    }
+    // outer iteration (Sec. 2.6): each pass builds the tree with the energy
+    // density of the previous pass (IF MAC, zeta_d) until delta < eps_lim
+    if ((rc = build(g, s, p, &t, st)) != TR_OK) return rc;     // allocates / sizes the tree
+    if (!t->e_work && (rc = dev_alloc(&t->e_work, 2 * sizeof(double) * (size_t)ncell, "iteration buffers")) != TR_OK)
+        return rc;
+    if (!t->dscratch && (rc = dev_alloc((unsigned char**)&t->dscratch, delta_scratch_bytes(), "delta state")) != TR_OK)
+        return rc;
+    double* e_old = t->e_work;
+    double* e_new = t->e_work + ncell;
+    if (g->e_prev) rc = cuda_check(cudaMemcpyAsync(e_old, g->e_prev, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, st), "copy e_prev");
+    else rc = cuda_check(cudaMemsetAsync(e_old, 0, sizeof(double) * ncell, st), "clear e");
+    if (rc != TR_OK) return rc;
+    int it = 0;
+    double delta = INFINITY;
+    while (it < p->max_iter) {
+        tr_grid gi = *g;
+        gi.e_prev = (it == 0 && !g->e_prev) ? nullptr : e_old;   // all-zero e is the same as none
+        if ((rc = build(&gi, s, p, &t, st)) != TR_OK) return rc;
+        WalkOut o;
+        o.F = F_out; o.e = e_new; o.ion = ion_out;
+        if ((rc = walk_run(t, nullptr, ncell, false, o, st)) != TR_OK) return rc;
+        if ((rc = read_status(t, st)) != TR_OK) return rc;
+        ++it;
+        if ((rc = delta_compute(e_new, e_old, ncell, p->delta_mode, t->dscratch, &delta, st)) != TR_OK) return rc;
+        double* tmp = e_old; e_old = e_new; e_new = tmp;
+        if (delta < p->eps_lim) break;
+    }
+    if (e_out && (rc = cuda_check(cudaMemcpyAsync(e_out, e_old, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, st),
+                                  "copy e")) != TR_OK)
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(st), "final copy")) != TR_OK) return rc;
+    if (iters_out) *iters_out = it;
+    if (delta_out) *delta_out = delta;
     return TR_OK;
+}
+
+tr_status tr_delta(const double* e_new, const double* e_old, int64_t n, int32_t delta_mode, double* delta_out,
+                   tr_stream stream) {
+    g_err[0] = '\0';
+    if (!e_new || !e_old || !delta_out || n < 1) return set_error(TR_EINVAL, "bad arguments to tr_delta");
+    if (delta_mode != 0 && delta_mode != 1) return set_error(TR_EINVAL, "delta_mode must be 0 or 1");
+    void* scratch = nullptr;
+    tr_status rc = dev_alloc((unsigned char**)&scratch, delta_scratch_bytes(), "delta state");
+    if (rc != TR_OK) return rc;
+    rc = delta_compute(e_new, e_old, n, delta_mode, scratch, delta_out, (cudaStream_t)stream);
+    cudaFree(scratch);
+    return rc;
 }
 
 tr_status tr_tree_info(const tr_tree* t, int64_t* n_nodes, int32_t* levels, int32_t* nr, int32_t* npix) {

@@ -97,6 +97,8 @@ struct tr_tree {
     const tr::Table* table = nullptr;
     tr::SweepTables sw;
     size_t nodes_bytes = 0;
+    double* e_work = nullptr;               // tr_solve iteration: 2 x N^3 energy densities
+    void* dscratch = nullptr;               // tr_solve iteration: delta reduction state
 };
 
 struct tr_rays {
@@ -151,5 +153,10 @@ tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, 
                    const WalkOut& out, cudaStream_t st);
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st);
 tr_status read_status(const tr_tree* t, cudaStream_t st);
+
+// iteration error control (tr_iter.cu)
+size_t delta_scratch_bytes();
+tr_status delta_compute(const double* e_new, const double* e_old, int64_t n, int mode, void* scratch, double* out,
+                        cudaStream_t st);
 
 }  // namespace tr

@@ -252,7 +252,7 @@ __device__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename 
     const int hi = min((int)ceil((real)a.eta * sqrt(real(2) * (d + reach))) + 1, nr - 1);
     real S = real(0);
     int first = hi + 1, last = lo - 1;
-    const bool keep = hi - lo + 1 <= MAXW;
+    const bool keep = MODE == 0 && hi - lo + 1 <= MAXW;
     for (int i = lo; i <= hi; ++i) {
         const real w = wp_kernel<real>(fabs(r[i] - d) * inv_h);
         if (keep) wrow[i - lo] = w;
@@ -494,7 +494,10 @@ __global__ void __launch_bounds__(NT) k_walk(WalkArgs a) {
     __shared__ int s_nacc;
     __shared__ RadialSpread<MODE> s_node[NT];                    // the step's nodes to spread
     __shared__ int s_pair0[NT + 1];                              // their first (node, ray) pair
-    __shared__ real s_w[NT * MAXW];                              // W_p values kept by the setup threads
+    // W_p values kept by the setup threads: the FP64 form saves recomputing
+    // them in FP64; in the FP32 form recomputing is cheaper than the shared
+    // memory (occupancy) they would take
+    __shared__ real s_w[MODE == 0 ? NT * MAXW : 1];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nr = a.nr, nbins = a.npix * nr;
     const int nq = a.use_e ? 3 : 2;
