@@ -42,9 +42,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-sample", type=int, default=3000, help="targets in the CPU-oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=6000, help="targets in the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--serving", type=int, default=24,
+                    help="requests in the continuous-batching serving run (0 skips it)")
+    ap.add_argument("--serving-sizes", default="32,64,128")
+    ap.add_argument("--serving-nsides", default="2")
+    ap.add_argument("--serving-rate", type=float, default=4.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -53,6 +58,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# ---------------------------------------------------------------- ranks
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of x over all ranks (the slowest rank sets the job's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, steps: int, max_total_ms: float, world: int) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / (max_total_ms * 1e-3)
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -227,18 +250,14 @@ def run_ours(args):
         return dict(step_ms=step_ms, walk_ms=walk_ms, stats=stats, info=info, wall=wall)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=devn)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, devn)
 
     # headline: FP32 moments + FP64 sweep, inputs resident
     with ClockSampler(local) as clk:
         r32 = timed_device(B.TR_FP32_SWEEP64, args.steps, args.warmup)
     total_ms = max_over_ranks(sum(r32["step_ms"]))
     ms_per_step = total_ms / args.steps
-    value = world * units * args.steps / (total_ms * 1e-3)
+    value = job_rate(units, args.steps, total_ms, world)
 
     # plain FP64 beside it
     k64 = args.fp64_steps if args.fp64_steps is not None else max(2, min(args.steps, 3))
@@ -302,7 +321,7 @@ def run_ours(args):
         "config": {"workload": f"{w.name}: {N}^3 log-normal (sigma_ln 1.5, k^-4), box 10 pc, "
                                f"{len(w.src_Q)} point sources, N_PIX={w.npix}, N_R={r32['info']['nr']}, "
                                f"theta_lim={w.theta_lim}",
-                   "precision": "FP32 node moments + compensated FP32 deposits, FP64 sweep",
+                   "precision": "FP32 node moments (compensated), FP32 deposits summed exactly in 64-bit fixed point, FP64 photon budget in the sweep",
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"independent problem per GPU x{world}"},
         "latency_ms": {"p50": statistics.median(r32["step_ms"]),
@@ -322,12 +341,33 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if args.serving > 0 and world == 1:
+        out["serving"] = serving_run(args)
     if pool is not None:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample, pool)
         pool.close()
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_run(args):
+    """Continuous batching of a Poisson stream of requests (serving loop)."""
+    from paper_2105_09644_gb300.serving import Server, poisson_stream, percentile
+    sizes = tuple(int(x) for x in args.serving_sizes.split(","))
+    nsides = tuple(int(x) for x in args.serving_nsides.split(","))
+    reqs = poisson_stream(args.serving, args.serving_rate, seed=2105, sizes=sizes, nsides=nsides, max_sources=1000)
+    srv = Server(budget_bytes=64 << 30, tick_targets=1 << 20, precision=1)
+    t0 = time.perf_counter()
+    done = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    lat = [1e3 * r.latency for r in done]
+    rays = sum(r.N ** 3 * 12 * r.nside * r.nside for r in done)
+    return {"requests": len(done), "arrival_rate_hz": args.serving_rate, "sizes": list(sizes),
+            "nsides": list(nsides), "sources": "1-1000 per request, log-uniform count",
+            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "max_ms": max(lat),
+            "cell_rays_per_s": rays / wall, "wall_s": wall, "launches": srv.launches,
+            "precision": "FP32 moments + FP64 sweep"}
 
 
 # ---------------------------------------------------------------- reference arm

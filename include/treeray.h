@@ -133,6 +133,21 @@ tr_status tr_ray_sweep(const tr_rays* r, double* F_out, double* e_out, uint8_t* 
 tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t* ion_out,
                         tr_stream stream);
 
+/* Continuous batching of independent problems: ONE persistent launch walks,
+ * maps and sweeps the targets of several built trees (different grid sizes,
+ * sources and N_PIX allowed; one precision per batch).  For tree i it does
+ * the cells whose Morton index (x bit 0, y bit 1, z bit 2 of each triple)
+ * lies in [first[i], first[i] + count[i]), writing F_out[i], e_out[i] and
+ * ion_out[i] at the cells' C-order indices (device arrays of that tree's
+ * N^3; the pointer arrays themselves are HOST arrays and may be NULL).  A
+ * serving loop admits requests between launches and splits large ones into
+ * Morton ranges, so that small requests are not held up by large ones.
+ * trees, first, count: HOST arrays of n >= 1 entries.  Synchronises
+ * `stream`.  Errors: TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_EOVERFLOW. */
+tr_status tr_walk_sweep_batch(const tr_tree* const* trees, const int64_t* first, const int64_t* count,
+                              int32_t n, double* const* F_out, double* const* e_out,
+                              uint8_t* const* ion_out, tr_stream stream);
+
 /* The fused fast path: build + walk + map + sweep for every cell, repeated
  * (Sec. 2.6) until delta < eps_lim or max_iter passes.  Outputs are N^3
  * device arrays (NULL allowed): F_out, e_out, ion_out as in tr_ray_sweep.

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_EINVAL", 2: "TR_ENOMEM", 3: "TR_ECUDA", 4: "T
 
 # every symbol include/treeray.h declares
 EXPORTED = ["tr_params_default", "tr_build_tree", "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve",
-            "tr_tree_stats", "tr_solve_noalloc", "tr_delta",
+            "tr_tree_stats", "tr_solve_noalloc", "tr_delta", "tr_walk_sweep_batch",
             "tr_tree_info", "tr_tree_nodes", "tr_rays_info", "tr_rays_export", "tr_table_info",
             "tr_table_export", "tr_tree_free", "tr_rays_free", "tr_last_error"]
 
@@ -69,6 +69,8 @@ def load():
     L.tr_ray_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_walk_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_tree_stats.argtypes = [vp, C.POINTER(i64)]
+    L.tr_walk_sweep_batch.argtypes = [C.POINTER(vp), C.POINTER(i64), C.POINTER(i64), i32, C.POINTER(vp),
+                                      C.POINTER(vp), C.POINTER(vp), vp]
     L.tr_delta.argtypes = [vp, vp, i64, i32, C.POINTER(C.c_double), vp]
     L.tr_solve_noalloc.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), vp, vp, vp, vp]
     L.tr_solve.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), vp, vp, vp,
@@ -204,6 +206,18 @@ def tr_solve(grid: Grid, sources: Sources, params: Params, F=None, e=None, ion=N
     check(load().tr_solve(C.byref(grid), C.byref(sources), C.byref(params), _ptr(F), _ptr(e), _ptr(ion),
                           C.byref(iters), C.byref(delta), _stream(stream)))
     return iters.value, delta.value
+
+
+def tr_walk_sweep_batch(trees, first, count, F=None, e=None, ion=None, stream=None):
+    """One persistent launch over target ranges of several trees (lists of equal length)."""
+    n = len(trees)
+    arr = lambda xs, t: (t * n)(*xs)
+    vp = C.c_void_p
+    Fp = arr([None if F is None or F[i] is None else F[i].data_ptr() for i in range(n)], vp)
+    ep = arr([None if e is None or e[i] is None else e[i].data_ptr() for i in range(n)], vp)
+    ip = arr([None if ion is None or ion[i] is None else ion[i].data_ptr() for i in range(n)], vp)
+    check(load().tr_walk_sweep_batch(arr([t.h.value for t in trees], vp), arr([int(x) for x in first], C.c_int64),
+                                     arr([int(x) for x in count], C.c_int64), n, Fp, ep, ip, _stream(stream)))
 
 
 def tr_delta(e_new, e_old, mode: int = 0, stream=None) -> float:

@@ -84,6 +84,7 @@ void tree_release(tr_tree* t) {
     cudaFree(t->status);
     cudaFree(t->stats);
     cudaFree(t->counter);
+    cudaFree(t->jobbuf);
     cudaFree(t->e_work);
     cudaFree(t->dscratch);
     sweep_tables_free(&t->sw);
@@ -126,7 +127,8 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
             (rc = dev_alloc(&t->ndot, sizeof(double) * (size_t)N * N * N, "cell emission")) != TR_OK ||
             (rc = dev_alloc(&t->status, 4 * sizeof(int32_t), "status words")) != TR_OK ||
             (rc = dev_alloc(&t->stats, 4 * sizeof(unsigned long long), "walk counters")) != TR_OK ||
-            (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK) {
+            (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK ||
+            (rc = dev_alloc((unsigned char**)&t->jobbuf, walk_job_bytes(1), "walk job record")) != TR_OK) {
             tree_release(t);
             return rc;
         }
@@ -278,6 +280,51 @@ tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t*
     tr_status rc = walk_run(t, nullptr, (int64_t)t->N * t->N * t->N, false, o, st);
     if (rc == TR_OK) rc = read_status(t, st);
     return rc;
+}
+
+namespace {
+struct BatchSpace {                          // per device: job records and work counter of batched walks
+    void* jobbuf = nullptr;
+    size_t bytes = 0;
+    unsigned int* counter = nullptr;
+};
+std::mutex g_batch_mu;
+std::map<int, BatchSpace> g_batch;
+}  // namespace
+
+tr_status tr_walk_sweep_batch(const tr_tree* const* trees, const int64_t* first, const int64_t* count, int32_t n,
+                              double* const* F_out, double* const* e_out, uint8_t* const* ion_out, tr_stream stream) {
+    g_err[0] = '\0';
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!trees || !first || !count || n < 1) return set_error(TR_EINVAL, "bad batch arguments");
+    int dev = 0;
+    tr_status rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc != TR_OK) return rc;
+    for (int i = 0; i < n; ++i) {
+        const tr_tree* t = trees[i];
+        if (!t) return set_error(TR_EINVAL, "tree %d is NULL", i);
+        if (t->device != dev) return set_error(TR_EINVAL, "tree %d lives on device %d, current is %d", i, t->device, dev);
+        if (t->mode != trees[0]->mode) return set_error(TR_EINVAL, "trees of one batch share a precision");
+        const int64_t ncell = (int64_t)t->N * t->N * t->N;
+        if (first[i] < 0 || count[i] < 0 || first[i] + count[i] > ncell)
+            return set_error(TR_EINVAL, "target range %d out of [0, N^3)", i);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchSpace& b = g_batch[dev];
+    const size_t need = walk_job_bytes(n);
+    if (b.bytes < need) {
+        cudaFree(b.jobbuf);
+        b.jobbuf = nullptr;
+        b.bytes = 0;
+        if ((rc = dev_alloc((unsigned char**)&b.jobbuf, need, "batch job records")) != TR_OK) return rc;
+        b.bytes = need;
+    }
+    if (!b.counter && (rc = dev_alloc(&b.counter, sizeof(unsigned int), "batch work counter")) != TR_OK) return rc;
+    if ((rc = walk_batch_run(trees, first, count, n, F_out, e_out, ion_out, b.jobbuf, b.counter, st)) != TR_OK)
+        return rc;
+    for (int i = 0; i < n; ++i)
+        if ((rc = read_status(trees[i], st)) != TR_OK) return rc;
+    return TR_OK;
 }
 
 tr_status tr_tree_stats(const tr_tree* t, int64_t* out4) {

@@ -97,6 +97,7 @@ struct tr_tree {
     const tr::Table* table = nullptr;
     tr::SweepTables sw;
     size_t nodes_bytes = 0;
+    void* jobbuf = nullptr;                 // device copy of the walk's job record
     double* e_work = nullptr;               // tr_solve iteration: 2 x N^3 energy densities
     void* dscratch = nullptr;               // tr_solve iteration: delta reduction state
 };
@@ -152,6 +153,10 @@ struct WalkOut {
 tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, bool dump,
                    const WalkOut& out, cudaStream_t st);
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st);
+size_t walk_job_bytes(int n_jobs);
+tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, const int64_t* count, int n,
+                         double* const* F, double* const* e, uint8_t* const* ion, void* jobbuf, unsigned int* counter,
+                         cudaStream_t st);
 tr_status read_status(const tr_tree* t, cudaStream_t st);
 
 // iteration error control (tr_iter.cu)

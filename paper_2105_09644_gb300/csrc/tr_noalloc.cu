@@ -25,7 +25,9 @@ constexpr size_t OFF_SUMS = up(OFF_NODES + sizeof(NodeF64) * NA_NNODES);
 constexpr size_t OFF_STATUS = up(OFF_SUMS + 3 * sizeof(double) * NA_NNODES);
 constexpr size_t OFF_STATS = up(OFF_STATUS + 4 * sizeof(int32_t));
 constexpr size_t OFF_COUNTER = up(OFF_STATS + 4 * sizeof(unsigned long long));
-constexpr size_t OFF_R = up(OFF_COUNTER + sizeof(unsigned int));
+constexpr size_t OFF_JOB = up(OFF_COUNTER + sizeof(unsigned int));
+constexpr size_t JOB_BYTES = 1024;                // one walk job record (checked at run time)
+constexpr size_t OFF_R = up(OFF_JOB + JOB_BYTES);
 constexpr size_t OFF_RF = up(OFF_R + sizeof(double) * MAX_NR);
 constexpr size_t OFF_INVR2 = up(OFF_RF + sizeof(float) * MAX_NR);
 constexpr size_t OFF_INVVOL = up(OFF_INVR2 + sizeof(double) * MAX_NR);
@@ -151,6 +153,8 @@ extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, con
     t.status = at<int32_t>(ds.base, OFF_STATUS);
     t.stats = at<unsigned long long>(ds.base, OFF_STATS);
     t.counter = at<unsigned int>(ds.base, OFF_COUNTER);
+    if (walk_job_bytes(1) > JOB_BYTES) return set_error(TR_EUNSUPPORTED, "walk job record larger than its slot");
+    t.jobbuf = ds.base + OFF_JOB;
     t.table = &ds.table;
     t.sw = ds.sw;
     t.p = *p;

@@ -16,6 +16,10 @@
 // Sweep (Sec. 2.5, Eq. 12-17): the bins become per-volume coefficients and
 // photon rates in FP64; each lane sweeps whole rays far to near and the warp
 // sums the rays (Eq. 18).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "tr_internal.cuh"
 
 namespace tr {
@@ -46,7 +50,8 @@ struct WalkArgs {
     const float* Gf;
     const float* ID2f;
     const float* GIf;
-    const int64_t* targets;                 // NULL: all cells, visited in Morton order
+    const int64_t* targets;                 // NULL: cells first .. first+n_targets-1 in Morton order
+    int64_t first;
     int64_t n_targets;
     double Fconv, Econv;                    // scaled flux -> CGS flux / energy density
     double* F;
@@ -61,7 +66,6 @@ struct WalkArgs {
     int acc_cap;
     int32_t* status;
     unsigned long long* stats;
-    unsigned int* counter;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -483,15 +487,38 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // One CTA of NT threads per target (persistent over targets).  Each step
 // pops NT/8 opened nodes and evaluates their NT children, one per thread.
+// Per-thread walk counters go to the job's counters (one atomic per warp).
+__device__ __forceinline__ void flush_counters(const WalkArgs& a, unsigned long long& n_vis, unsigned long long& n_acc,
+                                               unsigned long long& n_ent) {
+    for (int o = 16; o > 0; o >>= 1) {
+        n_vis += __shfl_xor_sync(FULL, n_vis, o);
+        n_acc += __shfl_xor_sync(FULL, n_acc, o);
+        n_ent += __shfl_xor_sync(FULL, n_ent, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.stats + 0, n_vis);
+        atomicAdd(a.stats + 1, n_acc);
+        atomicAdd(a.stats + 2, n_ent);
+    }
+    n_vis = n_acc = n_ent = 0;
+}
+
+// One CTA of NT threads per target, persistent over the targets of a list of
+// jobs (a job = one tree and a range or list of its cells).  Several trees in
+// one launch is how independent requests are batched together.  Each step
+// pops NT/8 opened nodes and evaluates their NT children, one per thread.
 template <int MODE, bool DUMP, int NT>
-__global__ void __launch_bounds__(NT) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
+                                            int n_jobs, unsigned int* counter) {
     using real = typename Prec<MODE>::real;
     constexpr int NW = NT / 32, P = NT / 8;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[NW], s_bcnt[NW], s_pcnt[NW];
     __shared__ double s_red[NW];
     __shared__ unsigned int s_q;
+    __shared__ int s_j;
     __shared__ int s_nacc;
+    __shared__ __align__(16) WalkArgs s_a;                       // the current job
     __shared__ RadialSpread<MODE> s_node[NT];                    // the step's nodes to spread
     __shared__ int s_pair0[NT + 1];                              // their first (node, ray) pair
     // W_p values kept by the setup threads: the FP64 form saves recomputing
@@ -499,38 +526,61 @@ __global__ void __launch_bounds__(NT) k_walk(WalkArgs a) {
     // memory (occupancy) they would take
     __shared__ real s_w[MODE == 0 ? NT * MAXW : 1];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nr = a.nr, nbins = a.npix * nr;
-    const int nq = a.use_e ? 3 : 2;
-    double* bins_a = reinterpret_cast<double*>(smem);
-    double* bins_eps = bins_a + nbins;
-    double* bins_e = a.use_e ? bins_eps + nbins : nullptr;
-    uint32_t* stack = reinterpret_cast<uint32_t*>(bins_a + (size_t)nq * nbins);
-    const int N = a.N, L = a.L;
+    const WalkArgs& a = s_a;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    const real* rr = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
     const real inv_m3 = real(1.0) / real(TM * TM * TM);
+    const int64_t total = job_end[n_jobs - 1];
     unsigned long long n_vis = 0, n_acc = 0, n_ent = 0;      // per-thread counters
+    int cur = -1;
+    int nr = 0, nbins = 0, nq = 2, N = 0, L = 0;
+    double *bins_a = nullptr, *bins_eps = nullptr, *bins_e = nullptr;
+    uint32_t* stack = nullptr;
+    const real* rr = nullptr;
     Scales sc{1.f, 1.f, 1.f};
-    if (MODE == 1) {                                         // fixed-point units from the root totals
-        real cm0[3], m0, q0[3], mi0;
-        load_node<MODE>(a.nodes, 0, cm0, m0, q0, mi0);
-        sc.a = fixed_scale((float)q0[0]);
-        sc.eps = fixed_scale((float)q0[1]);
-        sc.e = fixed_scale((float)q0[2]);
-    }
 
     for (;;) {
-        if (tid == 0) s_q = atomicAdd(a.counter, 1u);
+        if (tid == 0) {
+            const unsigned int qq = atomicAdd(counter, 1u);
+            int j = -1;
+            if ((int64_t)qq < total) { j = 0; while (job_end[j] <= (int64_t)qq) ++j; }
+            s_q = qq;
+            s_j = j;
+        }
         __syncthreads();
-        const int64_t q = (int64_t)s_q;
-        if (q >= a.n_targets) break;
+        const int j = s_j;
+        const int64_t qg = (int64_t)s_q;
+        if (j < 0) break;
+        if (j != cur) {                                          // load the job (uniform over the CTA)
+            if (cur >= 0) flush_counters(a, n_vis, n_acc, n_ent);
+            __syncthreads();
+            const int* src = reinterpret_cast<const int*>(jobs + j);
+            int* dst = reinterpret_cast<int*>(&s_a);
+            for (int k = tid; k < (int)(sizeof(WalkArgs) / sizeof(int)); k += NT) dst[k] = src[k];
+            __syncthreads();
+            cur = j;
+            nr = a.nr; nbins = a.npix * nr; nq = a.use_e ? 3 : 2; N = a.N; L = a.L;
+            bins_a = reinterpret_cast<double*>(smem);
+            bins_eps = bins_a + nbins;
+            bins_e = a.use_e ? bins_eps + nbins : nullptr;
+            stack = reinterpret_cast<uint32_t*>(bins_a + (size_t)nq * nbins);
+            rr = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
+            if (MODE == 1) {                                     // fixed-point units from the root totals
+                real cm0[3], m0, q0[3], mi0;
+                load_node<MODE>(a.nodes, 0, cm0, m0, q0, mi0);
+                sc.a = fixed_scale((float)q0[0]);
+                sc.eps = fixed_scale((float)q0[1]);
+                sc.e = fixed_scale((float)q0[2]);
+            }
+        }
+        const int64_t q = qg - (j > 0 ? job_end[j - 1] : 0);    // index within the job
         int tx, ty, tz;
         int64_t cell;
         if (a.targets) {
             cell = a.targets[q];
             tx = (int)(cell % N); ty = (int)((cell / N) % N); tz = (int)(cell / ((int64_t)N * N));
         } else {
-            tx = (int)compact3((uint32_t)q); ty = (int)compact3((uint32_t)q >> 1); tz = (int)compact3((uint32_t)q >> 2);
+            const uint32_t m = (uint32_t)(a.first + q);
+            tx = (int)compact3(m); ty = (int)compact3(m >> 1); tz = (int)compact3(m >> 2);
             cell = ((int64_t)tz * N + ty) * N + tx;
         }
         const real px = (real)tx + real(0.5), py = (real)ty + real(0.5), pz = (real)tz + real(0.5);
@@ -697,17 +747,7 @@ __global__ void __launch_bounds__(NT) k_walk(WalkArgs a) {
             if (a.ion) a.ion[o] = (uint8_t)(F > 0.0);
         }
     }
-    // kernel-wide counters, one atomic per warp
-    for (int o = 16; o > 0; o >>= 1) {
-        n_vis += __shfl_xor_sync(FULL, n_vis, o);
-        n_acc += __shfl_xor_sync(FULL, n_acc, o);
-        n_ent += __shfl_xor_sync(FULL, n_ent, o);
-    }
-    if (lane == 0) {
-        atomicAdd(a.stats + 0, n_vis);
-        atomicAdd(a.stats + 1, n_acc);
-        atomicAdd(a.stats + 2, n_ent);
-    }
+    if (cur >= 0) flush_counters(a, n_vis, n_acc, n_ent);
 }
 
 // Unfused sweep over bins stored by the dump walk: one CTA per target.
@@ -744,27 +784,6 @@ __global__ void __launch_bounds__(NT) k_sweep_stored(WalkArgs a, const double* b
 
 constexpr int WALK_NT = 128;                // threads per target (one CTA)
 
-WalkArgs make_args(const tr_tree* t) {
-    WalkArgs a{};
-    a.nodes = t->nodes;
-    a.N = t->N; a.L = t->L; a.nr = t->nr; a.npix = t->npix; a.eta = t->p.eta_r; a.nside = t->p.nside;
-    a.use_e = t->use_e;
-    a.th_lim2 = t->p.theta_lim * t->p.theta_lim;
-    a.th_if2 = t->p.theta_if * t->p.theta_if;
-    a.th_src2 = t->p.theta_src * t->p.theta_src;
-    a.lray = t->lray;
-    a.th_lim2f = (float)a.th_lim2; a.th_if2f = (float)a.th_if2; a.th_src2f = (float)a.th_src2;
-    a.lrayf = (float)t->lray;
-    a.toff = t->table->off; a.tent = t->table->ent; a.hdr = t->table->hdr;
-    a.r = t->sw.r; a.rf = t->sw.rf; a.inv_r2 = t->sw.inv_r2; a.inv_vol = t->sw.inv_vol; a.inv_volf = t->sw.inv_volf; a.G = t->sw.G; a.ID2 = t->sw.ID2; a.GI = t->sw.GI; a.Gf = t->sw.Gf; a.ID2f = t->sw.ID2f; a.GIf = t->sw.GIf;
-    a.Fconv = t->U / (t->dx * t->dx);
-    a.Econv = t->Eu;
-    a.status = t->status;
-    a.stats = t->stats;
-    a.counter = t->counter;
-    return a;
-}
-
 // Opened nodes waiting on a target's stack.  The stack never holds more
 // than the target's opened nodes (a few hundred at theta = 0.5); overflow
 // is detected and reported, never written past.
@@ -775,8 +794,31 @@ size_t walk_smem(const tr_tree* t) {
     return (size_t)nq * t->npix * t->nr * 8 + (size_t)STACK_CAP * 4;
 }
 
+WalkArgs make_args(const tr_tree* t) {
+    WalkArgs a{};
+    a.nodes = t->nodes;
+    a.N = t->N; a.L = t->L; a.nr = t->nr; a.npix = t->npix; a.eta = t->p.eta_r; a.nside = t->p.nside;
+    a.use_e = t->use_e;
+    a.stack_cap = STACK_CAP;
+    a.th_lim2 = t->p.theta_lim * t->p.theta_lim;
+    a.th_if2 = t->p.theta_if * t->p.theta_if;
+    a.th_src2 = t->p.theta_src * t->p.theta_src;
+    a.lray = t->lray;
+    a.th_lim2f = (float)a.th_lim2; a.th_if2f = (float)a.th_if2; a.th_src2f = (float)a.th_src2;
+    a.lrayf = (float)t->lray;
+    a.toff = t->table->off; a.tent = t->table->ent; a.hdr = t->table->hdr;
+    a.r = t->sw.r; a.rf = t->sw.rf; a.inv_r2 = t->sw.inv_r2; a.inv_vol = t->sw.inv_vol; a.inv_volf = t->sw.inv_volf;
+    a.G = t->sw.G; a.ID2 = t->sw.ID2; a.GI = t->sw.GI; a.Gf = t->sw.Gf; a.ID2f = t->sw.ID2f; a.GIf = t->sw.GIf;
+    a.Fconv = t->U / (t->dx * t->dx);
+    a.Econv = t->Eu;
+    a.status = t->status;
+    a.stats = t->stats;
+    return a;
+}
+
 template <typename K>
-tr_status launch_persistent(K kernel, size_t smem, const WalkArgs& a, cudaStream_t st) {
+tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
+                            int64_t total, unsigned int* counter, cudaStream_t st) {
     tr_status s = cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "cudaFuncSetAttribute(smem)");
     if (s != TR_OK) return s;
@@ -786,35 +828,80 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs& a, cudaStream
     s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WALK_NT, smem), "occupancy query");
     if (s != TR_OK) return s;
     if (per_sm < 1) return set_error(TR_EUNSUPPORTED, "ray bins need %zu bytes of shared memory per target", smem);
-    s = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st), "counter reset");
+    s = cuda_check(cudaMemsetAsync(counter, 0, sizeof(unsigned int), st), "counter reset");
     if (s != TR_OK) return s;
     int64_t blocks = (int64_t)sms * per_sm;
-    if (blocks > a.n_targets) blocks = a.n_targets > 0 ? a.n_targets : 1;
-    kernel<<<(unsigned)blocks, WALK_NT, smem, st>>>(a);
+    if (blocks > total) blocks = total > 0 ? total : 1;
+    kernel<<<(unsigned)blocks, WALK_NT, smem, st>>>(jobs, job_end, n_jobs, counter);
     return cuda_check(cudaGetLastError(), "walk kernel launch");
 }
 
+tr_status launch_jobs(int mode, bool dump, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
+                      int64_t total, unsigned int* counter, cudaStream_t st) {
+    if (mode == 0)
+        return dump ? launch_persistent(k_walk<0, true, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent(k_walk<0, false, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st);
+    return dump ? launch_persistent(k_walk<1, true, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st)
+                : launch_persistent(k_walk<1, false, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st);
+}
+
 }  // namespace
+
+size_t walk_job_bytes(int n_jobs) { return (size_t)n_jobs * (sizeof(WalkArgs) + sizeof(int64_t)); }
 
 tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, bool dump, const WalkOut& out,
                    cudaStream_t st) {
     WalkArgs a = make_args(t);
     a.targets = targets;
+    a.first = 0;
     a.n_targets = n_targets;
     a.F = out.F; a.E = out.e; a.ion = out.ion;
     a.bins_out = out.bins; a.ids_out = out.ids; a.counts_out = out.counts; a.eps_self_out = out.eps_self;
     a.scales_out = out.scales;
     a.acc_cap = out.acc_cap;
-    a.stack_cap = STACK_CAP;
-    const size_t smem = walk_smem(t);
+    // the job record goes to the tree's job buffer; the copy completes before
+    // return (host staging), so the stack record may go away afterwards
+    unsigned char host[sizeof(WalkArgs) + sizeof(int64_t)];
+    memcpy(host, &a, sizeof(WalkArgs));
+    memcpy(host + sizeof(WalkArgs), &n_targets, sizeof(int64_t));
     tr_status s = cuda_check(cudaMemsetAsync(t->status, 0, 4 * sizeof(int32_t), st), "status reset");
     if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
-    if (s != TR_OK) return s;
-    if (t->mode == 0)
-        s = dump ? launch_persistent(k_walk<0, true, WALK_NT>, smem, a, st) : launch_persistent(k_walk<0, false, WALK_NT>, smem, a, st);
-    else
-        s = dump ? launch_persistent(k_walk<1, true, WALK_NT>, smem, a, st) : launch_persistent(k_walk<1, false, WALK_NT>, smem, a, st);
-    return s;
+    if (s == TR_OK) s = cuda_check(cudaMemcpyAsync(t->jobbuf, host, sizeof host, cudaMemcpyHostToDevice, st), "job copy");
+    if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "job copy");
+    if (s != TR_OK || n_targets <= 0) return s;
+    const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(t->jobbuf);
+    const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<const unsigned char*>(t->jobbuf) + sizeof(WalkArgs));
+    return launch_jobs(t->mode, dump, walk_smem(t), jobs, job_end, 1, n_targets, t->counter, st);
+}
+
+tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, const int64_t* count, int n,
+                         double* const* F, double* const* e, uint8_t* const* ion, void* jobbuf, unsigned int* counter,
+                         cudaStream_t st) {
+    std::vector<unsigned char> host(walk_job_bytes(n));
+    WalkArgs* hj = reinterpret_cast<WalkArgs*>(host.data());
+    int64_t* he = reinterpret_cast<int64_t*>(host.data() + (size_t)n * sizeof(WalkArgs));
+    size_t smem = 0;
+    int64_t total = 0;
+    tr_status s = TR_OK;
+    for (int i = 0; i < n; ++i) {
+        WalkArgs a = make_args(trees[i]);
+        a.targets = nullptr;
+        a.first = first[i];
+        a.n_targets = count[i];
+        a.F = F ? F[i] : nullptr; a.E = e ? e[i] : nullptr; a.ion = ion ? ion[i] : nullptr;
+        hj[i] = a;
+        total += count[i];
+        he[i] = total;
+        smem = std::max(smem, walk_smem(trees[i]));
+        if (s == TR_OK) s = cuda_check(cudaMemsetAsync(trees[i]->status, 0, 4 * sizeof(int32_t), st), "status reset");
+        if (s == TR_OK) s = cuda_check(cudaMemsetAsync(trees[i]->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
+    }
+    if (s == TR_OK) s = cuda_check(cudaMemcpyAsync(jobbuf, host.data(), host.size(), cudaMemcpyHostToDevice, st), "job copy");
+    if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "job copy");
+    if (s != TR_OK || total == 0) return s;
+    const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(jobbuf);
+    const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<unsigned char*>(jobbuf) + (size_t)n * sizeof(WalkArgs));
+    return launch_jobs(trees[0]->mode, false, smem, jobs, job_end, n, total, counter, st);
 }
 
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st) {

@@ -1,0 +1,227 @@
+"""Serving loop: continuous batching of TreeRay/OnTheSpot requests on one GPU.
+
+Requests (a grid snapshot with its own sources and ray resolution) arrive
+over time.  The loop
+
+* admits waiting requests while their HBM footprint fits the budget (first
+  come first served, a smaller request may pass a larger one that does not
+  fit yet);
+* builds an admitted request's tree once and keeps it resident until the
+  request is done;
+* every tick, launches ONE persistent walk kernel (tr_walk_sweep_batch) over
+  a slice of the remaining target cells of every active request: requests
+  with the least remaining work get their slice first, large requests are cut
+  into Morton ranges so that they do not hold up small ones;
+* retires a request when its last slice is done and records its latency
+  (completion - arrival).
+
+The scheduling part (`Scheduler`) is plain Python without device calls, so
+it can be tested on the CPU; `Server` adds the device work through the C ABI.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float                      # seconds on the server clock
+    N: int
+    dx: float
+    n_H: np.ndarray                     # (N, N, N) float64
+    src_xyz: np.ndarray                 # (S, 3) float64 cm
+    src_Q: np.ndarray                   # (S,) float64 s^-1
+    nside: int = 2
+    theta_lim: float = 0.5
+    theta_src: float = math.inf
+    # filled by the server
+    admitted: float | None = None
+    done: float | None = None
+    next_target: int = 0
+    result: dict | None = None
+
+    @property
+    def n_targets(self) -> int:
+        return self.N ** 3
+
+    @property
+    def remaining(self) -> int:
+        return self.n_targets - self.next_target
+
+    @property
+    def latency(self) -> float | None:
+        return None if self.done is None else self.done - self.arrival
+
+
+def footprint_bytes(N: int, precision: int) -> int:
+    """Device bytes a request holds while resident: its tree (node records and
+    build sums), mapped emission, inputs and outputs."""
+    n_nodes = ((1 << (3 * (int(math.log2(N)) + 1))) - 1) // 7
+    rec = 64 if precision == 0 else 32
+    sums = 24 if precision == 0 else 12
+    cells = N ** 3
+    return n_nodes * (rec + sums) + cells * (8 + 8 + 8 + 8 + 1) + 4096
+
+
+class Scheduler:
+    """Admission by footprint and slicing of the active requests' targets."""
+
+    def __init__(self, budget_bytes: int, tick_targets: int, precision: int = 1, min_slice: int = 4096):
+        self.budget = budget_bytes
+        self.tick_targets = tick_targets
+        self.precision = precision
+        self.min_slice = min_slice
+        self.waiting: list[Request] = []
+        self.active: list[Request] = []
+        self.finished: list[Request] = []
+        self.in_use = 0
+
+    def submit(self, req: Request):
+        self.waiting.append(req)
+
+    def admit(self, now: float) -> list[Request]:
+        admitted = []
+        for req in list(self.waiting):
+            fp = footprint_bytes(req.N, self.precision)
+            if fp > self.budget:
+                raise ValueError(f"request {req.rid} needs {fp} bytes, more than the whole budget {self.budget}")
+            if self.in_use + fp <= self.budget:
+                self.waiting.remove(req)
+                self.active.append(req)
+                self.in_use += fp
+                req.admitted = now
+                admitted.append(req)
+        return admitted
+
+    def plan(self) -> list[tuple[Request, int, int]]:
+        """Slices (request, first Morton index, count) for one launch: least
+        remaining work first, at most tick_targets in total."""
+        left = self.tick_targets
+        out = []
+        for req in sorted(self.active, key=lambda r: (r.remaining, r.arrival)):
+            if left <= 0:
+                break
+            take = min(req.remaining, max(left, self.min_slice))
+            if take > 0:
+                out.append((req, req.next_target, take))
+                left -= take
+        return out
+
+    def complete(self, slices, now: float) -> list[Request]:
+        done = []
+        for req, first, count in slices:
+            assert first == req.next_target
+            req.next_target += count
+            if req.remaining == 0:
+                req.done = now
+                self.active.remove(req)
+                self.in_use -= footprint_bytes(req.N, self.precision)
+                self.finished.append(req)
+                done.append(req)
+        return done
+
+    def idle(self) -> bool:
+        return not self.waiting and not self.active
+
+
+class Server:
+    """Scheduler plus the device work (tree builds and batched walks)."""
+
+    def __init__(self, budget_bytes: int, tick_targets: int = 1 << 20, precision: int = 1, device=None):
+        import torch
+        from . import binding as B
+        self.B = B
+        self.torch = torch
+        self.dev = device or torch.device("cuda")
+        self.sched = Scheduler(budget_bytes, tick_targets, precision)
+        self.precision = precision
+        self.state: dict[int, dict] = {}
+        self.t0 = time.perf_counter()
+        self.launches = 0
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, req: Request):
+        self.sched.submit(req)
+
+    def _start(self, req: Request):
+        torch, B = self.torch, self.B
+        d = dict(n_H=torch.from_numpy(np.ascontiguousarray(req.n_H)).to(self.dev),
+                 xyz=torch.from_numpy(np.ascontiguousarray(req.src_xyz)).to(self.dev),
+                 Q=torch.from_numpy(np.ascontiguousarray(req.src_Q)).to(self.dev))
+        shape = (req.N,) * 3
+        d["F"] = torch.empty(shape, dtype=torch.float64, device=self.dev)
+        d["e"] = torch.empty_like(d["F"])
+        d["ion"] = torch.empty(shape, dtype=torch.uint8, device=self.dev)
+        p = B.tr_params_default(nside=req.nside, theta_lim=req.theta_lim, theta_src=req.theta_src,
+                                precision=self.precision)
+        d["tree"] = B.tr_build_tree(B.make_grid(d["n_H"], req.dx), B.make_sources(d["xyz"], d["Q"]), p)
+        self.state[req.rid] = d
+
+    def _finish(self, req: Request):
+        d = self.state.pop(req.rid)
+        req.result = dict(F=d["F"].cpu().numpy(), e=d["e"].cpu().numpy(), ion=d["ion"].cpu().numpy())
+
+    def tick(self) -> int:
+        """Admit, launch one batch, retire; returns the number of targets done."""
+        for req in self.sched.admit(self.now()):
+            self._start(req)
+        slices = self.sched.plan()
+        if not slices:
+            return 0
+        st = [self.state[r.rid] for r, _, _ in slices]
+        self.B.tr_walk_sweep_batch([d["tree"] for d in st], [f for _, f, _ in slices], [c for _, _, c in slices],
+                                   [d["F"] for d in st], [d["e"] for d in st], [d["ion"] for d in st])
+        self.launches += 1
+        for req in self.sched.complete(slices, self.now()):
+            self._finish(req)
+        return sum(c for _, _, c in slices)
+
+    def run(self, requests: list[Request]) -> list[Request]:
+        """Replay requests at their arrival times (seconds after start)."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        self.t0 = time.perf_counter()
+        i = 0
+        while i < len(pending) or not self.sched.idle():
+            now = self.now()
+            while i < len(pending) and pending[i].arrival <= now:
+                self.submit(pending[i])
+                i += 1
+            if self.tick() == 0 and i < len(pending):
+                time.sleep(max(0.0, min(0.002, pending[i].arrival - self.now())))
+        return self.sched.finished
+
+
+def poisson_stream(n: int, rate_hz: float, seed: int, sizes=(32, 64, 128, 256), nsides=(2, 4),
+                   max_sources: int = 1000, box_pc: float = 10.0) -> list[Request]:
+    """Seeded request stream: Poisson arrivals, grid size uniform over `sizes`,
+    log-normal k^-4 density, 1..max_sources sources (log-uniform count)."""
+    from workloads import PC_CM, lognormal_density, uniform_sources
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        N = int(rng.choice(sizes))
+        nside = int(rng.choice(nsides))
+        S = int(round(10 ** rng.uniform(0.0, math.log10(max_sources))))
+        box = box_pc * PC_CM
+        rho = lognormal_density(N, seed * 1000 + k)
+        xyz, q = uniform_sources(S, box, seed * 1000 + k + 500, 46.0, 49.0)
+        out.append(Request(k, t, N, box / N, rho, xyz, q, nside=nside,
+                           theta_lim=0.5 if nside == 2 else 0.25))
+    return out
+
+
+def percentile(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(math.ceil(p / 100.0 * len(xs))) - 1))
+    return xs[k]
