@@ -404,73 +404,154 @@ __device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, con
     return F0;
 }
 
-// The sweep of the FP32 form: the deposits (alpha, e) and the geometric
+// The sweep of the FP32 form.  The deposits (alpha, e) and the geometric
 // factors are FP32 quantities, so each segment's loss R_ij (Eq. 14) is formed
-// in FP32; the photon budget Phi_j from which the losses are subtracted, and
-// which cancels at the ionisation front, is kept and updated in FP64.
-__device__ __forceinline__ bool dpos(double v) { return __double_as_longlong(v) > 0; }   // v > 0
+// in FP32.  The emitted budget E_j = eps_j / 4pi (Eq. 12) and the running loss
+// L_j = sum of R_ij are carried as unevaluated sums of two FP32 numbers
+// (hi + lo, about 48 significant bits; L by compensated addition), so that
+// the per-segment work needs no FP64 instruction -- on GB300 FP64 runs at
+// 1/54 of the FP32 rate and would make the sweep cost grow with the number
+// of sources on a ray.  A source is spent when L_j reaches E_j
+// (Phi = max(E - L, 0), Eq. 13).  The cancellation Phi_j = E_j - L_j that
+// decides the flux near the ionisation front, the flux F_0 (Eq. 10-11) and
+// hence the ionised/neutral classification are done in FP64 at the end of
+// the ray.  E_j lives in the eps slot of point j and L_j in the alpha slot
+// of point j, which the sweep has consumed by the time source j starts.
+__device__ __forceinline__ float2 two_sum(float a, float b) {    // Knuth: a + b = s + e exactly
+    const float s = a + b;
+    const float bp = s - a;
+    const float e = (a - (s - bp)) + (b - bp);
+    return make_float2(s, e);
+}
 
-template <>
-__device__ double sweep_ray<1>(const WalkArgs& a, const double* ba, double* be, const double* bee, const Scales& sc) {
+__device__ __forceinline__ float phi_f(const float2 E, const float2 Lr) {  // E - L to FP32 precision
+    return (E.x - Lr.x) + (E.y - Lr.y);
+}
+
+// FP32-form sweep of one ray by a group of SG lanes of one warp (gmask):
+// lane gl owns the ray's source points j with j % SG == gl and keeps their
+// budgets and losses; the total flux of each segment (for zeta_s, zeta_d) is
+// summed over the group with shuffles.  All lanes of the group return F_0.
+constexpr int SG = 4;
+constexpr uint64_t SG_PATTERN = 0x1111111111111111ull;   // bits j with j % 4 == 0
+
+__device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* be, const double* bee,
+                                  const Scales& sc, int gl, unsigned gmask) {
     const int nr = a.nr;
     uint64_t m0 = 0, m1 = 0;
-    for (int j = 1; j < nr; ++j) {
-        if (bin_nonzero<1>(be + j)) {
-            if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64);
-        }
+    for (int j = 1 + ((gl + SG - 1) % SG); j < nr; j += SG) {   // lane gl scans j == gl (mod SG)
+        if (bin_nonzero<1>(be + j)) { if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64); }
+    }
+    for (int o = 1; o < SG; o <<= 1) {
+        m0 |= __shfl_xor_sync(gmask, m0, o);
+        m1 |= __shfl_xor_sync(gmask, m1, o);
     }
     if (!(m0 | m1)) return 0.0;
+    const uint64_t sel = SG_PATTERN << gl;                    // 64 % SG == 0: same pattern for m1
+    const uint64_t o0 = m0 & sel, o1 = m1 & sel;
     const double inv4pi = 1.0 / (4.0 * PI_D);
-    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; be[j] = bin_value<1>(be + j, sc.eps) * inv4pi; }
-    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; be[j] = bin_value<1>(be + j, sc.eps) * inv4pi; }
-    double* ph = be;                                              // Eq. 12
+    float2* E = reinterpret_cast<float2*>(be);
+    float2* Ls = reinterpret_cast<float2*>(const_cast<double*>(ba));
+    for (int half = 0; half < 2; ++half)
+        for (uint64_t w = half ? o1 : o0; w; w &= w - 1) {
+            const int j = (half ? 64 : 0) + __ffsll((long long)w) - 1;
+            const double v = bin_value<1>(be + j, sc.eps) * inv4pi;   // Eq. 12
+            const float hi = (float)v;
+            E[j] = make_float2(hi, (float)(v - (double)hi));
+        }
     const float ia = 1.0f / sc.a, ie = 1.0f / sc.e;
     const int jtop = m1 ? 64 + 63 - __clzll((long long)m1) : 63 - __clzll((long long)m0);
     float a_hi = bin_value_f<1>(ba + jtop, ia) * __ldg(a.inv_volf + jtop);
-    for (int i = jtop - 1; i >= 0 && (m0 | m1); --i) {
+    __syncwarp(gmask);                                        // alpha at jtop read before any overwrite
+    uint64_t d0 = 0, d1 = 0;                                  // own spent sources
+    for (int i = jtop - 1; i >= 0; --i) {
+        if (!__any_sync(gmask, ((o0 & ~d0) | (o1 & ~d1)) != 0ull)) break;
         const float a_lo = bin_value_f<1>(ba + i, ia) * __ldg(a.inv_volf + i);
-        const int b = i + 1;
-        const uint64_t a0 = (b < 64) ? (m0 & (~0ull << b)) : 0ull;
-        const uint64_t a1 = (b <= 64) ? m1 : (m1 & (~0ull << (b - 64)));
-        if (a0 | a1) {
+        __syncwarp(gmask);                                    // everyone has read alpha_i
+        const int b = i + 1;                                  // source b starts: its loss slot was alpha_b
+        if (((b < 64 ? (o0 >> b) : (o1 >> (b - 64))) & 1ull)) Ls[b] = make_float2(0.f, 0.f);
+        const uint64_t a0 = (b < 64) ? (o0 & ~d0 & (~0ull << b)) : 0ull;
+        const uint64_t a1 = (b <= 64) ? (o1 & ~d1) : (o1 & ~d1 & (~0ull << (b - 64)));
+        const float* id2 = a.ID2f + (size_t)i * nr;
+        float Fl = 0.f;
+        for (int half = 0; half < 2; ++half)
+            for (uint64_t w = half ? a1 : a0; w; w &= w - 1) {
+                const int j = (half ? 64 : 0) + __ffsll((long long)w) - 1;
+                Fl = fmaf(phi_f(E[j], Ls[j]), __ldg(id2 + j), Fl);
+            }
+        int cnt = __popcll((long long)a0) + __popcll((long long)a1);
+        for (int o = 1; o < SG; o <<= 1) {
+            Fl += __shfl_xor_sync(gmask, Fl, o);
+            cnt += __shfl_xor_sync(gmask, cnt, o);
+        }
+        if (cnt > 0) {
             const float A = 0.5f * (a_lo + a_hi);
-            if (!bee && __popcll((long long)a0) + __popcll((long long)a1) == 1) {
-                const int j = a0 ? __ffsll((long long)a0) - 1 : 64 + __ffsll((long long)a1) - 1;
-                const double np = ph[j] - (double)(A * __ldg(a.Gf + (size_t)i * nr + j));      // Eq. 13-14
-                if (dpos(np)) ph[j] = np;
-                else { ph[j] = 0.0; if (j < 64) m0 &= ~(1ull << j); else m1 &= ~(1ull << (j - 64)); }
-            } else {
-                const float* id2 = a.ID2f + (size_t)i * nr;
-                const float* gi = a.GIf + (size_t)i * nr;
-                float Ftot = 0.f;                                 // Eq. 11 at the segment midpoint
-                for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Ftot = fmaf((float)ph[j], __ldg(id2 + j), Ftot); }
-                for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Ftot = fmaf((float)ph[j], __ldg(id2 + j), Ftot); }
-                if (Ftot > 0.f) {
-                    float zd = 1.f;                               // Eq. 17
+            const bool single = !bee && cnt == 1;             // zeta_s = 1, zeta_d = 1
+            float cf = 0.f;
+            bool go = true;
+            if (!single) {
+                if (Fl > 0.f) {
+                    float zd = 1.f;                           // Eq. 17
                     if (bee) {
                         const float ev = bin_value_f<1>(bee + i + 1, ie) * __ldg(a.inv_volf + i + 1);
-                        if (ev > 0.f) zd = fminf(2.f, Ftot / ev);
+                        if (ev > 0.f) zd = fminf(2.f, Fl / ev);
                     }
-                    const float cf = A * zd / Ftot;               // zeta_s = F_j / Ftot (Eq. 16)
-                    for (uint64_t w = a0; w; w &= w - 1) {
-                        const int j = __ffsll((long long)w) - 1;
-                        const double np = ph[j] - (double)(cf * (__ldg(gi + j) * (float)ph[j]));   // Eq. 13-14
-                        if (dpos(np)) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
-                    }
-                    for (uint64_t w = a1; w; w &= w - 1) {
-                        const int j = 64 + __ffsll((long long)w) - 1;
-                        const double np = ph[j] - (double)(cf * (__ldg(gi + j) * (float)ph[j]));
-                        if (dpos(np)) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
-                    }
+                    cf = A * zd / Fl;                         // zeta_s = F_j / Ftot (Eq. 16)
+                } else {
+                    go = false;
                 }
+            }
+            if (go) {
+                const float* gi = a.GIf + (size_t)i * nr;
+                const float* g = a.Gf + (size_t)i * nr;
+                for (int half = 0; half < 2; ++half)
+                    for (uint64_t w = half ? a1 : a0; w; w &= w - 1) {
+                        const int j = (half ? 64 : 0) + __ffsll((long long)w) - 1;
+                        const float2 e = E[j];
+                        const float2 L = Ls[j];
+                        const float R = single ? A * __ldg(g + j) : cf * (__ldg(gi + j) * phi_f(e, L));   // Eq. 14
+                        const float2 t = two_sum(L.x, R);     // compensated L += R
+                        const float2 Ln = two_sum(t.x, t.y + L.y);
+                        if (phi_f(e, Ln) > 0.f) Ls[j] = Ln;
+                        else if (half) d1 |= 1ull << (j - 64); else d0 |= 1ull << j;   // spent: Phi = 0
+                    }
             }
         }
         a_hi = a_lo;
     }
-    double F0 = 0.0;                                              // Eq. 10-11 at r = 0
-    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
-    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
+    double F0 = 0.0;                                          // Eq. 10-11 at r = 0, in FP64
+    for (int half = 0; half < 2; ++half)
+        for (uint64_t w = half ? (o1 & ~d1) : (o0 & ~d0); w; w &= w - 1) {
+            const int j = (half ? 64 : 0) + __ffsll((long long)w) - 1;
+            const float2 e = E[j];
+            const float2 L = Ls[j];
+            const double phi = ((double)e.x + (double)e.y) - ((double)L.x + (double)L.y);
+            if (phi > 0.0) F0 = fma(phi, __ldg(a.inv_r2 + j), F0);
+        }
+    for (int o = 1; o < SG; o <<= 1) F0 += __shfl_xor_sync(gmask, F0, o);
     return F0;
+}
+
+// Sum over the rays of one target (Eq. 18): FP64 form one thread per ray,
+// FP32 form one group of SG lanes per ray.
+template <int MODE, int NT>
+__device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, double* bins_eps, double* bins_e,
+                                             const Scales& sc) {
+    const int nr = a.nr, tid = threadIdx.x;
+    double Fk = 0.0;
+    if (MODE == 0) {
+        for (int k = tid; k < a.npix; k += NT)
+            Fk += sweep_ray<0>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
+    } else {
+        const int gl = tid % SG, lane = tid & 31;
+        const unsigned gmask = ((1u << SG) - 1u) << (lane & ~(SG - 1));
+        for (int k = tid / SG; k < a.npix; k += NT / SG) {
+            const double f = sweep_ray_group(a, bins_a + k * nr, bins_eps + k * nr,
+                                             a.use_e ? bins_e + k * nr : nullptr, sc, gl, gmask);
+            if (gl == 0) Fk += f;
+        }
+    }
+    return Fk;
 }
 
 template <int NT>
@@ -736,9 +817,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             }
             continue;
         }
-        double Fk = 0.0;
-        for (int k = tid; k < a.npix; k += NT)
-            Fk += sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
+        const double Fk = sweep_rays<MODE, NT>(a, bins_a, bins_eps, bins_e, sc);
         const double F = block_sum<NT>(Fk, s_red) + eps_self / (4.0 * PI_D * 0.25);
         if (tid == 0) {
             const int64_t o = a.targets ? q : cell;
@@ -769,10 +848,8 @@ __global__ void __launch_bounds__(NT) k_sweep_stored(WalkArgs a, const double* b
             if (a.use_e) bins_e[b] = in[2 * nbins + b];
         }
         __syncthreads();
-        double Fk = 0.0;
-        for (int k = tid; k < a.npix; k += NT)
-            Fk += sweep_ray<MODE>(a, bins_a + k * a.nr, bins_eps + k * a.nr, a.use_e ? bins_e + k * a.nr : nullptr,
-                                  Scales{a.scales_in[0], a.scales_in[1], a.scales_in[2]});
+        const double Fk = sweep_rays<MODE, NT>(a, bins_a, bins_eps, bins_e,
+                                               Scales{a.scales_in[0], a.scales_in[1], a.scales_in[2]});
         const double F = block_sum<NT>(Fk, s_red) + eps_self[q] / (4.0 * PI_D * 0.25);
         if (tid == 0) {
             if (a.F) a.F[q] = F * a.Fconv;

@@ -282,3 +282,19 @@ def test_full_size_turbulent128_sampled(B, orc, precision):
     # sampled cells may sit at a front; require the bar on all but a front-sized fraction
     assert np.mean(err <= RTOL[precision]) >= 0.97, (np.sort(err)[-5:])
     assert np.mean(ion[targets] == ion_orc) >= 0.97
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["sourcecount256_s100", "sourcecount256_s10000"])
+def test_full_size_sourcecount256_sampled(B, orc, name):
+    """The 256^3 source-count workloads (30 pc box, N_R = 59), FP32 form,
+    sampled targets against the oracle."""
+    w = workload(name)
+    F, e, ion = gpu_solve(B, w, 1)
+    rng = np.random.default_rng(256)
+    targets = rng.integers(0, w.N ** 3, 80)
+    F_orc, _, ion_orc = orc.Tree(w).solve_pass(orc.params_for(w), targets=targets)
+    lit = F_orc > 0
+    err = np.abs(F[targets][lit] - F_orc[lit]) / F_orc[lit]
+    assert np.mean(err <= RTOL[1]) >= 0.97, (np.sort(err)[-5:])
+    assert np.mean(ion[targets] == ion_orc) >= 0.97
