@@ -78,6 +78,11 @@ def lib():
             L.orc_tree_build.restype = C.c_void_p
             L.orc_tree_build.argtypes = [C.c_int32, C.c_double, C.c_double, _D, _D, _D,
                                          C.c_int32, _D, _D, _D]
+            L.orc_tree_build_amr.restype = C.c_void_p
+            L.orc_tree_build_amr.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _D, C.c_int32,
+                                             _I32, _I32, _D, _D, C.c_int32, _D, _D, _D]
+            L.orc_tree_n_leaves.restype = C.c_int64
+            L.orc_tree_n_leaves.argtypes = [C.c_void_p]
             L.orc_tree_free.argtypes = [C.c_void_p]
             L.orc_tree_levels.restype = C.c_int32
             L.orc_tree_levels.argtypes = [C.c_void_p]
@@ -165,8 +170,10 @@ def sweep_ray(alpha_vol, eps, e_vol=None, *, eta_r=2, nside=2, zeta_g=True, kd=0
 
 
 def params_for(w, *, zeta_g: bool = True, lray_cells: float = 0.0, **over) -> Params:
-    """Oracle parameters for a :class:`workloads.Workload` (overrides by keyword)."""
-    d = dict(N=w.N, dx_cm=w.dx, nside=w.nside, eta_r=w.eta_r, theta_lim=w.theta_lim,
+    """Oracle parameters for a :class:`workloads.Workload` or an AMR grid
+    (lengths in finest cells there; overrides by keyword)."""
+    N, dx = (w.N_fine, w.dx_fine) if hasattr(w, "N_fine") else (w.N, w.dx)
+    d = dict(N=N, dx_cm=dx, nside=w.nside, eta_r=w.eta_r, theta_lim=w.theta_lim,
              theta_if=w.theta_if, theta_src=w.theta_src, lray_cells=lray_cells,
              alpha_B=w.alpha_B, hnu=w.hnu, zeta_g=int(zeta_g))
     d.update(over)
@@ -185,6 +192,7 @@ class Tree:
         self.h = lib().orc_tree_build(w.N, w.dx, w.alpha_B, _p(lo), _p(nH), _p(nd),
                                       int(q.shape[0]), _p(xyz), _p(q), _p(ep))
         self.use_e = e_prev is not None
+        self.n_leaf = w.N ** 3
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -201,7 +209,7 @@ class Tree:
         return out
 
     def cell_quantities(self):
-        nc = self.N ** 3
+        nc = self.n_leaf
         nd, a, e = np.zeros(nc), np.zeros(nc), np.zeros(nc)
         lib().orc_cell_quantities(self.h, _p(nd), _p(a), _p(e))
         return nd, a, e
@@ -222,7 +230,7 @@ class Tree:
 
     def solve_pass(self, p: Params, targets=None):
         if targets is None:
-            n = self.N ** 3
+            n = self.n_leaf
             tp = None
         else:
             targets = np.ascontiguousarray(targets, dtype=np.int64)
@@ -231,6 +239,25 @@ class Tree:
         F, e, ion = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.uint8)
         lib().orc_solve_pass(self.h, C.byref(p), tp, n, _p(F), _p(e), _p(ion, _U8))
         return F, e, ion
+
+
+class AmrTree(Tree):
+    """Oracle octree over an AMR grid of 8^3-cell blocks (Sec. 2.1): targets
+    and per-cell arrays are indexed b * 512 + c, c = (iz * 8 + iy) * 8 + ix."""
+
+    def __init__(self, g, e_prev=None, box_lo=(0.0, 0.0, 0.0), ndot_cell=None):
+        self.N = g.N_fine
+        lev = np.ascontiguousarray(g.blk_level, dtype=np.int32)
+        pos = np.ascontiguousarray(g.blk_pos, dtype=np.int32).reshape(-1)
+        self._keep = [lev, pos, _f64(g.n_H).ravel(), _f64(ndot_cell).ravel() if ndot_cell is not None else None,
+                      _f64(g.src_xyz).reshape(-1), _f64(g.src_Q),
+                      _f64(e_prev).ravel() if e_prev is not None else None, np.asarray(box_lo, dtype=np.float64)]
+        lev, pos, nH, nd, xyz, q, ep, lo = self._keep
+        self.h = lib().orc_tree_build_amr(g.N_base, g.max_level, g.dx_fine, g.alpha_B, _p(lo), int(lev.shape[0]),
+                                          _p(lev, _I32), _p(pos, _I32), _p(nH), _p(nd), int(q.shape[0]),
+                                          _p(xyz), _p(q), _p(ep))
+        self.use_e = e_prev is not None
+        self.n_leaf = int(lib().orc_tree_n_leaves(self.h))
 
 
 def solve(w, p: Params, *, e_init=None, max_iter: int = 1, eps_lim: float = 1e-2,

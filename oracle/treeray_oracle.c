@@ -46,6 +46,10 @@
  *  R8 zeta_g is applied literally (Eq. 16) behind a switch.
  *  R9 delta_cell (Eq. 21) and delta_tot (Eq. 20) use absolute differences;
  *     the median is the lower median.
+ *  R10 AMR grids: lengths are in cells of the finest level; a cell of edge
+ *     s (finest cells) has volume s^3 and mass n_H s^3; the target sphere of
+ *     such a cell has r_tp = s/2; a parent sums its eight children, and a
+ *     leaf (an AMR cell) is never opened.
  */
 #include "treeray_oracle.h"
 
@@ -329,15 +333,42 @@ typedef struct {
     double alpha, eps, e, mion;
 } orc_node;
 
+enum { ORC_UNUSED = 0, ORC_LEAF = 1, ORC_INTERNAL = 2 };
+
 struct orc_tree {
-    int32_t N, L;
-    double dx_cm;
+    int32_t N, L;           /* N = cells per axis of the finest level */
+    double dx_cm;           /* finest cell edge */
     int use_e;
     orc_node** lv;          /* lv[l] has (2^l)^3 nodes, index (iz*n + iy)*n + ix */
+    uint8_t** flag;         /* AMR: per node ORC_LEAF / ORC_INTERNAL / ORC_UNUSED; NULL: uniform */
+    int64_t n_leaf;         /* cells (targets): N^3 uniform, blocks x 512 AMR */
+    int8_t* leaf_lev;       /* AMR: tree level of each cell */
+    int32_t* leaf_pos;      /* AMR: 3 per cell, position at that level */
     double* ndot;           /* per-cell emission rate after source mapping */
     double* alpha_c;        /* per-cell clipped recombination rate (Eq. 2) */
     double* eps_c;          /* per-cell clipped emission rate (Eq. 1) */
 };
+
+static int node_flag(const orc_tree* t, int32_t level, int64_t idx)
+{
+    if (!t->flag) return level == t->L ? ORC_LEAF : ORC_INTERNAL;
+    return t->flag[level][idx];
+}
+
+/* level, position (at that level) and edge (finest cells) of target cell q */
+static void target_geom(const orc_tree* t, int64_t q, int32_t* lev, int64_t* p3, int64_t* edge)
+{
+    if (!t->flag) {
+        int64_t N = t->N;
+        *lev = t->L;
+        p3[0] = q % N; p3[1] = (q / N) % N; p3[2] = q / (N * N);
+        *edge = 1;
+        return;
+    }
+    *lev = t->leaf_lev[q];
+    for (int a = 0; a < 3; ++a) p3[a] = t->leaf_pos[3 * q + a];
+    *edge = (int64_t)(t->N >> *lev);
+}
 
 static int64_t lidx(int64_t n, int64_t ix, int64_t iy, int64_t iz) { return (iz * n + iy) * n + ix; }
 
@@ -351,6 +382,7 @@ orc_tree* orc_tree_build(int32_t N, double dx_cm, double alpha_B, const double* 
     while ((1 << L) < N) L++;
     t->N = N; t->L = L; t->dx_cm = dx_cm; t->use_e = (e_prev != NULL);
     int64_t nc = (int64_t)N * N * N;
+    t->n_leaf = nc;
     t->ndot = (double*)calloc((size_t)nc, sizeof(double));
     t->alpha_c = (double*)calloc((size_t)nc, sizeof(double));
     t->eps_c = (double*)calloc((size_t)nc, sizeof(double));
@@ -435,10 +467,135 @@ orc_tree* orc_tree_build(int32_t N, double dx_cm, double alpha_B, const double* 
     return t;
 }
 
+static int32_t ilog2(int64_t v) { int32_t l = 0; while (((int64_t)1 << l) < v) ++l; return l; }
+
+orc_tree* orc_tree_build_amr(int32_t N_base, int32_t max_level, double dx_fine_cm, double alpha_B,
+                             const double* box_lo_cm, int32_t n_blocks, const int32_t* blk_level,
+                             const int32_t* blk_pos, const double* n_H, const double* ndot_cell,
+                             int32_t nsrc, const double* src_xyz_cm, const double* src_Q, const double* e_prev)
+{
+    orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
+    int32_t N = N_base << max_level, L = ilog2(N), Lb = ilog2(N_base);
+    t->N = N; t->L = L; t->dx_cm = dx_fine_cm; t->use_e = (e_prev != NULL);
+    int64_t nl = (int64_t)n_blocks * 512;
+    t->n_leaf = nl;
+    t->ndot = (double*)calloc((size_t)nl, sizeof(double));
+    t->alpha_c = (double*)calloc((size_t)nl, sizeof(double));
+    t->eps_c = (double*)calloc((size_t)nl, sizeof(double));
+    t->leaf_lev = (int8_t*)malloc((size_t)nl);
+    t->leaf_pos = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)nl);
+    t->lv = (orc_node**)calloc((size_t)L + 1, sizeof(orc_node*));
+    t->flag = (uint8_t**)calloc((size_t)L + 1, sizeof(uint8_t*));
+    int32_t** leafid = (int32_t**)calloc((size_t)L + 1, sizeof(int32_t*));
+    for (int32_t l = 0; l <= L; ++l) {
+        int64_t n = (int64_t)1 << l;
+        t->lv[l] = (orc_node*)calloc((size_t)(n * n * n), sizeof(orc_node));
+        t->flag[l] = (uint8_t*)calloc((size_t)(n * n * n), 1);
+        leafid[l] = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * n * n));
+    }
+    /* the cells of every block are the leaves */
+    for (int32_t b = 0; b < n_blocks; ++b) {
+        int32_t lc = Lb + blk_level[b];
+        int64_t n = (int64_t)1 << lc;
+        for (int c = 0; c < 512; ++c) {
+            int64_t q = (int64_t)b * 512 + c;
+            int64_t ix = 8 * (int64_t)blk_pos[3 * b + 0] + (c & 7);
+            int64_t iy = 8 * (int64_t)blk_pos[3 * b + 1] + ((c >> 3) & 7);
+            int64_t iz = 8 * (int64_t)blk_pos[3 * b + 2] + (c >> 6);
+            t->leaf_lev[q] = (int8_t)lc;
+            t->leaf_pos[3 * q + 0] = (int32_t)ix; t->leaf_pos[3 * q + 1] = (int32_t)iy; t->leaf_pos[3 * q + 2] = (int32_t)iz;
+            t->flag[lc][lidx(n, ix, iy, iz)] = ORC_LEAF;
+            leafid[lc][lidx(n, ix, iy, iz)] = (int32_t)q;
+            if (ndot_cell) t->ndot[q] = ndot_cell[q];
+        }
+    }
+    /* point sources to the cell containing them (reading R2 on the finest lattice) */
+    for (int32_t s = 0; s < nsrc; ++s) {
+        int64_t f[3];
+        for (int a = 0; a < 3; ++a) {
+            double v = floor((src_xyz_cm[3 * s + a] - box_lo_cm[a]) / dx_fine_cm);
+            if (v < 0.0) v = 0.0;
+            if (v > N - 1) v = N - 1;
+            f[a] = (int64_t)v;
+        }
+        for (int32_t l = 0; l <= L; ++l) {
+            int64_t n = (int64_t)1 << l, sh = L - l;
+            int64_t id = lidx(n, f[0] >> sh, f[1] >> sh, f[2] >> sh);
+            if (t->flag[l][id] == ORC_LEAF) { t->ndot[leafid[l][id]] += src_Q[s]; break; }
+        }
+    }
+    /* leaves: Eq. 1-3 per cell of edge s (volume s^3 finest cells) */
+    double dvf = dx_fine_cm * dx_fine_cm * dx_fine_cm;
+    for (int64_t q = 0; q < nl; ++q) {
+        int32_t lc = t->leaf_lev[q];
+        int64_t n = (int64_t)1 << lc;
+        double s = (double)(N >> lc), vol = s * s * s;
+        double rec = alpha_B * (n_H[q] * n_H[q]) * (dvf * vol);
+        t->eps_c[q] = fmax(t->ndot[q] - rec, 0.0);
+        t->alpha_c[q] = fmax(rec - t->ndot[q], 0.0);
+        orc_node* nd = &t->lv[lc][lidx(n, t->leaf_pos[3 * q], t->leaf_pos[3 * q + 1], t->leaf_pos[3 * q + 2])];
+        nd->m = n_H[q] * vol;
+        nd->smx = nd->m * (((double)t->leaf_pos[3 * q + 0] + 0.5) * s);
+        nd->smy = nd->m * (((double)t->leaf_pos[3 * q + 1] + 0.5) * s);
+        nd->smz = nd->m * (((double)t->leaf_pos[3 * q + 2] + 0.5) * s);
+        nd->alpha = t->alpha_c[q];
+        nd->eps = t->eps_c[q];
+        nd->e = e_prev ? e_prev[q] * vol : 0.0;
+        nd->mion = (e_prev && e_prev[q] > 0.0) ? nd->m : 0.0;
+    }
+    /* parents: the sum of their eight children, in Morton order */
+    for (int32_t l = L - 1; l >= 0; --l) {
+        int64_t n = (int64_t)1 << l;
+        for (int64_t iz = 0; iz < n; ++iz)
+            for (int64_t iy = 0; iy < n; ++iy)
+                for (int64_t ix = 0; ix < n; ++ix) {
+                    int64_t id = lidx(n, ix, iy, iz);
+                    if (t->flag[l][id] == ORC_LEAF) continue;
+                    if (t->flag[l + 1][lidx(2 * n, 2 * ix, 2 * iy, 2 * iz)] == ORC_UNUSED) continue;
+                    t->flag[l][id] = ORC_INTERNAL;
+                    orc_node* p = &t->lv[l][id];
+                    for (int ch = 0; ch < 8; ++ch) {
+                        const orc_node* q = &t->lv[l + 1][lidx(2 * n, 2 * ix + (ch & 1), 2 * iy + ((ch >> 1) & 1),
+                                                               2 * iz + ((ch >> 2) & 1))];
+                        if (ch == 0) {
+                            p->m = q->m; p->smx = q->smx; p->smy = q->smy; p->smz = q->smz;
+                            p->alpha = q->alpha; p->eps = q->eps; p->e = q->e; p->mion = q->mion;
+                        } else {
+                            p->m += q->m; p->smx += q->smx; p->smy += q->smy; p->smz += q->smz;
+                            p->alpha += q->alpha; p->eps += q->eps; p->e += q->e; p->mion += q->mion;
+                        }
+                    }
+                }
+    }
+    for (int32_t l = 0; l <= L; ++l) {
+        int64_t n = (int64_t)1 << l;
+        double s = (double)(N >> l);
+        for (int64_t iz = 0; iz < n; ++iz)
+            for (int64_t iy = 0; iy < n; ++iy)
+                for (int64_t ix = 0; ix < n; ++ix) {
+                    orc_node* p = &t->lv[l][lidx(n, ix, iy, iz)];
+                    if (p->m > 0.0) {
+                        p->cm[0] = p->smx / p->m; p->cm[1] = p->smy / p->m; p->cm[2] = p->smz / p->m;
+                    } else {
+                        p->cm[0] = ((double)ix + 0.5) * s;
+                        p->cm[1] = ((double)iy + 0.5) * s;
+                        p->cm[2] = ((double)iz + 0.5) * s;
+                    }
+                }
+    }
+    for (int32_t l = 0; l <= L; ++l) free(leafid[l]);
+    free(leafid);
+    return t;
+}
+
+int64_t orc_tree_n_leaves(const orc_tree* t) { return t->n_leaf; }
+
 void orc_tree_free(orc_tree* t)
 {
     if (!t) return;
     for (int32_t l = 0; l <= t->L; ++l) free(t->lv[l]);
+    if (t->flag) for (int32_t l = 0; l <= t->L; ++l) free(t->flag[l]);
+    free(t->flag); free(t->leaf_lev); free(t->leaf_pos);
     free(t->lv); free(t->ndot); free(t->alpha_c); free(t->eps_c); free(t);
 }
 
@@ -453,7 +610,7 @@ void orc_tree_node(const orc_tree* t, int32_t level, int64_t ix, int64_t iy, int
 
 void orc_cell_quantities(const orc_tree* t, double* ndot_out, double* alpha_out, double* eps_out)
 {
-    int64_t nc = (int64_t)t->N * t->N * t->N;
+    int64_t nc = t->n_leaf;
     for (int64_t c = 0; c < nc; ++c) {
         if (ndot_out) ndot_out[c] = t->ndot[c];
         if (alpha_out) alpha_out[c] = t->alpha_c[c];
@@ -482,7 +639,9 @@ static int64_t canonical_id(int32_t level, int64_t ix, int64_t iy, int64_t iz)
 typedef struct {
     const orc_tree* t;
     const orc_params* p;
-    int64_t tx, ty, tz;
+    int64_t tx, ty, tz;       /* target corner, finest cells */
+    int64_t ts;               /* target edge, finest cells */
+    double cx, cy, cz;        /* target centre */
     int32_t nr;
     double lray;
     double th_lim2, th_if2, th_src2;
@@ -502,9 +661,9 @@ static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t
     if (nd->alpha == 0.0 && nd->eps == 0.0 && (!use_e || nd->e == 0.0)) return;
     if (d > w->lray) return;                       /* beyond the maximum ray length (R6) */
     int64_t s = (int64_t)(w->t->N >> level);
-    int64_t ox = 2 * ix * s + s - 2 * w->tx - 1;   /* 2 x (geometric centre - target centre) */
-    int64_t oy = 2 * iy * s + s - 2 * w->ty - 1;
-    int64_t oz = 2 * iz * s + s - 2 * w->tz - 1;
+    int64_t ox = 2 * ix * s + s - 2 * w->tx - w->ts;   /* 2 x (geometric centre - target centre) */
+    int64_t oy = 2 * iy * s + s - 2 * w->ty - w->ts;
+    int64_t oz = 2 * iz * s + s - 2 * w->tz - w->ts;
     const orc_entry* ent = table_entry(p->nside, orc_table_key(ox, oy, oz, s));
     int32_t nr = w->nr;
     double h = (double)s;
@@ -529,20 +688,21 @@ static void walk_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_
     int64_t n = (int64_t)1 << level;
     const orc_node* nd = &t->lv[level][lidx(n, ix, iy, iz)];
     int64_t s = (int64_t)(t->N >> level);
+    int fl = node_flag(t, level, lidx(n, ix, iy, iz));
     w->visited++;
     int contains = (w->tx >= ix * s && w->tx < ix * s + s) && (w->ty >= iy * s && w->ty < iy * s + s) &&
                    (w->tz >= iz * s && w->tz < iz * s + s);
     if (contains) {
-        if (level == t->L) return;                 /* the target itself (R3) */
+        if (fl == ORC_LEAF) return;                /* the target itself (R3) */
         for (int ch = 0; ch < 8; ++ch)
             walk_node(w, level + 1, 2 * ix + (ch & 1), 2 * iy + ((ch >> 1) & 1), 2 * iz + ((ch >> 2) & 1));
         return;
     }
-    double dx = ((double)w->tx + 0.5) - nd->cm[0];
-    double dy = ((double)w->ty + 0.5) - nd->cm[1];
-    double dz = ((double)w->tz + 0.5) - nd->cm[2];
+    double dx = w->cx - nd->cm[0];
+    double dy = w->cy - nd->cm[1];
+    double dz = w->cz - nd->cm[2];
     double d2 = (dx * dx + dy * dy) + dz * dz;
-    if (level < t->L) {
+    if (fl != ORC_LEAF) {
         double h2 = (double)s * (double)s;
         int acc_lim = h2 < w->th_lim2 * d2;                               /* BH MAC */
         int is_if = (DELTA_IF * nd->m < nd->mion) && (nd->mion < (1.0 - DELTA_IF) * nd->m);
@@ -566,8 +726,15 @@ int64_t orc_walk_target(const orc_tree* t, const orc_params* p, int64_t target,
     walk_ctx w;
     memset(&w, 0, sizeof w);
     w.t = t; w.p = p;
-    int64_t N = t->N;
-    w.tx = target % N; w.ty = (target / N) % N; w.tz = target / (N * N);
+    {
+        int32_t tl;
+        int64_t p3[3], edge;
+        target_geom(t, target, &tl, p3, &edge);
+        w.tx = p3[0] * edge; w.ty = p3[1] * edge; w.tz = p3[2] * edge; w.ts = edge;
+        w.cx = (double)w.tx + 0.5 * (double)edge;
+        w.cy = (double)w.ty + 0.5 * (double)edge;
+        w.cz = (double)w.tz + 0.5 * (double)edge;
+    }
     w.lray = lray_of(p);
     w.nr = orc_num_points(p->eta_r, w.lray);
     w.th_lim2 = p->theta_lim * p->theta_lim;
@@ -645,7 +812,7 @@ double orc_sweep_ray(int32_t nr, int32_t eta_r, int32_t nside, int32_t zeta_g,
 int32_t orc_solve_pass(const orc_tree* t, const orc_params* p, const int64_t* targets,
                        int64_t n_targets, double* F_out, double* e_out, uint8_t* ion_out)
 {
-    int64_t N = t->N, nc = N * N * N;
+    int64_t nc = t->n_leaf;
     double lray = lray_of(p);
     int32_t nr = orc_num_points(p->eta_r, lray);
     int64_t npix = 12 * (int64_t)p->nside * p->nside;
@@ -678,7 +845,13 @@ int32_t orc_solve_pass(const orc_tree* t, const orc_params* p, const int64_t* ta
             F += orc_sweep_ray(nr, p->eta_r, p->nside, p->zeta_g, av, &be[k * nr],
                                bee ? ev : NULL, kd, NULL, NULL);
         }
-        F += t->eps_c[tgt] / (4.0 * ORC_PI * 0.25);   /* own emission, r_tp = dx/2 (R3) */
+        {
+            int32_t tl;
+            int64_t p3[3], edge;
+            target_geom(t, tgt, &tl, p3, &edge);
+            double rtp = 0.5 * (double)edge;
+            F += t->eps_c[tgt] / (4.0 * ORC_PI * (rtp * rtp));   /* own emission, r_tp = half the cell (R3) */
+        }
         double Fphys = F / dx2;
         if (F_out) F_out[q] = Fphys;
         if (e_out) e_out[q] = Fphys * p->hnu / C_LIGHT;   /* Eq. 18 */

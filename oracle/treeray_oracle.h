@@ -66,6 +66,15 @@ orc_tree* orc_tree_build(int32_t N, double dx_cm, double alpha_B, const double* 
                          const double* n_H, const double* ndot_cell,
                          int32_t nsrc, const double* src_xyz_cm, const double* src_Q,
                          const double* e_prev);
+/* AMR grid: n_blocks blocks of 8^3 cells; block b has refinement level
+ * blk_level[b] (cell edge = (N_base << max_level) >> (log2 N_base + level)
+ * finest cells) and corner blk_pos[3b..3b+2] in units of its own edge;
+ * cell arrays are [b][iz][iy][ix]; targets are cell indices b*512 + c. */
+orc_tree* orc_tree_build_amr(int32_t N_base, int32_t max_level, double dx_fine_cm, double alpha_B,
+                             const double* box_lo_cm, int32_t n_blocks, const int32_t* blk_level,
+                             const int32_t* blk_pos, const double* n_H, const double* ndot_cell,
+                             int32_t nsrc, const double* src_xyz_cm, const double* src_Q, const double* e_prev);
+int64_t orc_tree_n_leaves(const orc_tree* t);
 void orc_tree_free(orc_tree* t);
 int32_t orc_tree_levels(const orc_tree* t);
 /* out8 = {m, cm_x, cm_y, cm_z, alpha, eps, e, m_ion} */

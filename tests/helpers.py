@@ -36,3 +36,14 @@ def decode_id(cid):
         iy |= ((m >> (3 * b + 1)) & 1) << b
         iz |= ((m >> (3 * b + 2)) & 1) << b
     return level, ix, iy, iz
+
+
+def amr_cells(g):
+    """Corner (finest cells, [x, y, z]) and edge of every cell of an AMR grid,
+    indexed b * 512 + (iz * 8 + iy) * 8 + ix: the layout of its blocks only."""
+    size = np.array([g.cell_size(b) for b in range(g.n_blocks)], dtype=np.int64)
+    c = np.arange(512)
+    local = np.stack([c & 7, (c >> 3) & 7, c >> 6], axis=1)               # [x, y, z]
+    corner = (8 * g.blk_pos.astype(np.int64)[:, None, :] + local[None, :, :]) * size[:, None, None]
+    return corner.reshape(-1, 3), np.repeat(size, 512)
+
