@@ -91,6 +91,31 @@ typedef struct {
     const double* Q;        /* device, n EUV photon rates, s^-1 */
 } tr_sources;
 
+/* AMR grid of blocks of 8^3 cells (Sec. 2.1: every block is a subtree of
+ * the octree whose leaves are the cells).  Block b has refinement level
+ * blk_level[b] in [0, max_level] (its cells have edge
+ * 2^(max_level - blk_level[b]) finest cells) and corner
+ * (blk_pos[3b], blk_pos[3b+1], blk_pos[3b+2]) = (x, y, z) in units of its
+ * own edge (8 of its cells).  The blocks must tile the box exactly once.
+ * N_base (base-level cells per axis) is a power of two >= 8 and
+ * N_base << max_level <= 512.  blk_level and blk_pos are HOST arrays (the
+ * library copies them); cell arrays are DEVICE arrays of n_blocks x 512
+ * values, [b][iz][iy][ix] within each block, and a cell's index (target,
+ * output position) is b * 512 + (iz * 8 + iy) * 8 + ix.  n_H, ndot and
+ * e_prev mean what they mean in tr_grid. */
+typedef struct {
+    int32_t N_base;
+    int32_t max_level;
+    int32_t n_blocks;
+    const int32_t* blk_level;   /* host, n_blocks */
+    const int32_t* blk_pos;     /* host, 3 x n_blocks */
+    double box_lo[3];           /* low corner of the box, cm */
+    double dx_fine;             /* edge of a cell of level max_level, cm */
+    const double* n_H;
+    const double* ndot;
+    const double* e_prev;
+} tr_amr_grid;
+
 typedef struct tr_tree tr_tree;
 typedef struct tr_rays tr_rays;
 
@@ -108,8 +133,28 @@ void tr_params_default(tr_params* p);
 tr_status tr_build_tree(const tr_grid* g, const tr_sources* s, const tr_params* p,
                         tr_tree** out, tr_stream stream);
 
-/* Walk the tree for n_targets target cells (C-order cell indices, device
- * int64 array; NULL with n_targets = N^3 means every cell) and map the
+/* Build the octree of an AMR grid (Sec. 2.1, Eq. 1-3).  The tree spans the
+ * finest lattice (N_base << max_level cells per axis) in the same
+ * level-order Morton numbering as a uniform tree; a node is a cell (leaf,
+ * never opened), a parent of eight existing nodes, or absent (inside a
+ * cell).  Lengths inside are in finest cells: a cell of edge s has volume
+ * s^3, mass n_H s^3, and its own emission reaches it through a sphere of
+ * radius s/2 (Sec. 2.5).  Point sources go to the cell that contains them.
+ * The walk calls (tr_walk_map, tr_walk_sweep, tr_walk_sweep_batch) then
+ * take cell indices b * 512 + c as targets and write outputs indexed the
+ * same way; targets of tr_walk_sweep_batch ranges are in walk order
+ * (blocks sorted along the Morton curve of the finest lattice, cells in
+ * Morton order inside a block).  *out may hold an earlier tree: it is
+ * freed and replaced.  The block layout is checked on the host: levels and
+ * positions in range, no block inside another, total volume = box.
+ * Synchronises `stream` (the block tables are copied from the host).
+ * Errors: TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_EUNSUPPORTED. */
+tr_status tr_build_tree_amr(const tr_amr_grid* g, const tr_sources* s, const tr_params* p,
+                            tr_tree** out, tr_stream stream);
+
+/* Walk the tree for n_targets target cells (C-order cell indices, or
+ * b * 512 + c on an AMR tree; device int64 array; NULL with n_targets = the
+ * number of cells means every cell) and map the
  * accepted nodes onto each target's rays (Sec. 2.3-2.4).  The result keeps,
  * per target, the ray bins alpha/eps/e ([N_PIX][N_R] each) and the list of
  * accepted node ids (level-order Morton numbering: (8^l - 1)/7 + Morton
@@ -128,8 +173,10 @@ tr_status tr_ray_sweep(const tr_rays* r, double* F_out, double* e_out, uint8_t* 
 
 /* Walk + map + sweep for every cell of a built tree in one fused kernel
  * (Sec. 2.3-2.5, Eq. 18): the ray bins of each target stay in shared memory.
- * Outputs as in tr_ray_sweep, N^3 device arrays in C order (NULL allowed).
- * Synchronises `stream`.  Errors: TR_EINVAL, TR_ECUDA, TR_EOVERFLOW. */
+ * Outputs as in tr_ray_sweep, one value per cell (N^3 in C order, or
+ * n_blocks x 512 on an AMR tree; NULL allowed).  Synchronises `stream`.
+ * Errors: TR_EINVAL, TR_ECUDA, TR_EOVERFLOW, TR_EUNSUPPORTED (ray bins
+ * larger than a CTA's shared memory). */
 tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t* ion_out,
                         tr_stream stream);
 
@@ -139,7 +186,9 @@ tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t*
  * the cells whose Morton index (x bit 0, y bit 1, z bit 2 of each triple)
  * lies in [first[i], first[i] + count[i]), writing F_out[i], e_out[i] and
  * ion_out[i] at the cells' C-order indices (device arrays of that tree's
- * N^3; the pointer arrays themselves are HOST arrays and may be NULL).  A
+ * N^3; the pointer arrays themselves are HOST arrays and may be NULL); on
+ * an AMR tree the range is in its walk order and outputs are indexed
+ * b * 512 + c (see tr_build_tree_amr).  A
  * serving loop admits requests between launches and splits large ones into
  * Morton ranges, so that small requests are not held up by large ones.
  * trees, first, count: HOST arrays of n >= 1 entries.  Synchronises
@@ -196,6 +245,14 @@ tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, const tr_param
 /* Sizes of a tree: node count, levels (log2 N + 1), N_R, N_PIX. Host outputs. */
 tr_status tr_tree_info(const tr_tree* t, int64_t* n_nodes, int32_t* levels,
                        int32_t* nr, int32_t* npix);
+
+/* Number of cells (targets) of a tree: N^3, or n_blocks x 512 for an AMR
+ * tree.  Host output. */
+tr_status tr_tree_cells(const tr_tree* t, int64_t* n_cells);
+
+/* Topology of a tree, one byte per node in level-order Morton numbering
+ * (device array of n_nodes): 0 absent, 1 leaf (a cell), 2 parent. */
+tr_status tr_tree_flags(const tr_tree* t, uint8_t* out, tr_stream stream);
 
 /* Counters of the last walk over this tree (host output, 4 values):
  * nodes visited, nodes accepted, table entries read, deepest stack. */

@@ -83,6 +83,8 @@ def lib():
                                              _I32, _I32, _D, _D, C.c_int32, _D, _D, _D]
             L.orc_tree_n_leaves.restype = C.c_int64
             L.orc_tree_n_leaves.argtypes = [C.c_void_p]
+            L.orc_tree_flag.restype = C.c_int32
+            L.orc_tree_flag.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64]
             L.orc_tree_free.argtypes = [C.c_void_p]
             L.orc_tree_levels.restype = C.c_int32
             L.orc_tree_levels.argtypes = [C.c_void_p]
@@ -202,6 +204,10 @@ class Tree:
     @property
     def levels(self) -> int:
         return int(lib().orc_tree_levels(self.h))
+
+    def flag(self, level, ix, iy, iz) -> int:
+        """1 leaf (a cell), 2 parent, 0 inside a cell."""
+        return int(lib().orc_tree_flag(self.h, level, ix, iy, iz))
 
     def node(self, level, ix, iy, iz) -> np.ndarray:
         out = np.zeros(8)

@@ -590,6 +590,13 @@ orc_tree* orc_tree_build_amr(int32_t N_base, int32_t max_level, double dx_fine_c
 
 int64_t orc_tree_n_leaves(const orc_tree* t) { return t->n_leaf; }
 
+/* 1 for a leaf (a grid cell), 2 for a parent, 0 for a position inside a cell */
+int32_t orc_tree_flag(const orc_tree* t, int32_t level, int64_t ix, int64_t iy, int64_t iz)
+{
+    int64_t n = (int64_t)1 << level;
+    return node_flag(t, level, lidx(n, ix, iy, iz));
+}
+
 void orc_tree_free(orc_tree* t)
 {
     if (!t) return;

@@ -75,6 +75,7 @@ orc_tree* orc_tree_build_amr(int32_t N_base, int32_t max_level, double dx_fine_c
                              const int32_t* blk_pos, const double* n_H, const double* ndot_cell,
                              int32_t nsrc, const double* src_xyz_cm, const double* src_Q, const double* e_prev);
 int64_t orc_tree_n_leaves(const orc_tree* t);
+int32_t orc_tree_flag(const orc_tree* t, int32_t level, int64_t ix, int64_t iy, int64_t iz);
 void orc_tree_free(orc_tree* t);
 int32_t orc_tree_levels(const orc_tree* t);
 /* out8 = {m, cm_x, cm_y, cm_z, alpha, eps, e, m_ion} */

@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_EINVAL", 2: "TR_ENOMEM", 3: "TR_ECUDA", 4: "T
                 5: "TR_EUNSUPPORTED", 6: "TR_EOVERFLOW"}
 
 # every symbol include/treeray.h declares
-EXPORTED = ["tr_params_default", "tr_build_tree", "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve",
+EXPORTED = ["tr_params_default", "tr_build_tree", "tr_build_tree_amr", "tr_tree_cells", "tr_tree_flags",
+            "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve",
             "tr_tree_stats", "tr_solve_noalloc", "tr_delta", "tr_walk_sweep_batch",
             "tr_tree_info", "tr_tree_nodes", "tr_rays_info", "tr_rays_export", "tr_table_info",
             "tr_table_export", "tr_tree_free", "tr_rays_free", "tr_last_error"]
@@ -45,6 +46,12 @@ class Grid(C.Structure):
                 ("n_H", C.c_void_p), ("ndot", C.c_void_p), ("e_prev", C.c_void_p)]
 
 
+class AmrGrid(C.Structure):
+    _fields_ = [("N_base", C.c_int32), ("max_level", C.c_int32), ("n_blocks", C.c_int32),
+                ("blk_level", C.c_void_p), ("blk_pos", C.c_void_p), ("box_lo", C.c_double * 3),
+                ("dx_fine", C.c_double), ("n_H", C.c_void_p), ("ndot", C.c_void_p), ("e_prev", C.c_void_p)]
+
+
 class Sources(C.Structure):
     _fields_ = [("n", C.c_int32), ("xyz", C.c_void_p), ("Q", C.c_void_p)]
 
@@ -65,6 +72,9 @@ def load():
     L.tr_params_default.argtypes = [C.POINTER(Params)]
     L.tr_params_default.restype = None
     L.tr_build_tree.argtypes = [C.POINTER(Grid), C.POINTER(Sources), C.POINTER(Params), C.POINTER(vp), vp]
+    L.tr_build_tree_amr.argtypes = [C.POINTER(AmrGrid), C.POINTER(Sources), C.POINTER(Params), C.POINTER(vp), vp]
+    L.tr_tree_cells.argtypes = [vp, C.POINTER(i64)]
+    L.tr_tree_flags.argtypes = [vp, vp, vp]
     L.tr_walk_map.argtypes = [vp, vp, i64, C.POINTER(vp), vp]
     L.tr_ray_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_walk_sweep.argtypes = [vp, vp, vp, vp, vp]
@@ -129,6 +139,26 @@ def make_grid(n_H, dx: float, box_lo=(0.0, 0.0, 0.0), ndot=None, e_prev=None) ->
                 None if ndot is None else ndot.data_ptr(), None if e_prev is None else e_prev.data_ptr())
 
 
+def make_amr_grid(N_base: int, max_level: int, blk_level, blk_pos, n_H, dx_fine: float, box_lo=(0.0, 0.0, 0.0),
+                  ndot=None, e_prev=None):
+    """AMR grid: blk_level (B,) and blk_pos (B, 3) host integer arrays, cell
+    arrays device float64 tensors of B x 512 values.  Returns the struct and
+    the host arrays it points to (keep both alive for the call)."""
+    import numpy as np
+    lev = np.ascontiguousarray(blk_level, dtype=np.int32)
+    pos = np.ascontiguousarray(blk_pos, dtype=np.int32).reshape(-1)
+    B = int(lev.shape[0])
+    assert pos.shape[0] == 3 * B
+    for t in (n_H, ndot, e_prev):
+        if t is not None:
+            assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+            assert t.numel() == B * 512
+    g = AmrGrid(int(N_base), int(max_level), B, lev.ctypes.data, pos.ctypes.data, (C.c_double * 3)(*box_lo),
+                float(dx_fine), n_H.data_ptr(), None if ndot is None else ndot.data_ptr(),
+                None if e_prev is None else e_prev.data_ptr())
+    return g, (lev, pos)
+
+
 def make_sources(xyz=None, Q=None) -> Sources:
     if xyz is None or Q is None or Q.numel() == 0:
         return Sources(0, None, None)
@@ -174,6 +204,24 @@ def tr_build_tree(grid: Grid, sources: Sources, params: Params, tree: Tree | Non
     tree = tree or Tree()
     check(load().tr_build_tree(C.byref(grid), C.byref(sources), C.byref(params), C.byref(tree.h), _stream(stream)))
     return tree
+
+
+def tr_build_tree_amr(grid, sources: Sources, params: Params, tree: Tree | None = None, stream=None) -> Tree:
+    """grid: the (struct, host arrays) pair of make_amr_grid."""
+    g, _keep = grid
+    tree = tree or Tree()
+    check(load().tr_build_tree_amr(C.byref(g), C.byref(sources), C.byref(params), C.byref(tree.h), _stream(stream)))
+    return tree
+
+
+def tr_tree_cells(tree: Tree) -> int:
+    n = C.c_int64()
+    check(load().tr_tree_cells(tree.h, C.byref(n)))
+    return n.value
+
+
+def tr_tree_flags(tree: Tree, out, stream=None):
+    check(load().tr_tree_flags(tree.h, _ptr(out), _stream(stream)))
 
 
 def tr_walk_map(tree: Tree, targets=None, n_targets: int | None = None, stream=None) -> Rays:

@@ -4,8 +4,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
+#include <unordered_set>
+#include <utility>
+#include <vector>
 
 #include "tr_internal.cuh"
 
@@ -87,6 +91,10 @@ void tree_release(tr_tree* t) {
     cudaFree(t->jobbuf);
     cudaFree(t->e_work);
     cudaFree(t->dscratch);
+    cudaFree(t->flags);
+    cudaFree(t->blk);
+    cudaFree(t->blk_order);
+    cudaFree(t->blkmap);
     sweep_tables_free(&t->sw);
     delete t;
 }
@@ -110,7 +118,7 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
     const size_t rec = mode == 0 ? sizeof(NodeF64) : sizeof(NodeF32);
     const size_t sum_bytes = (size_t)n_nodes * 3 * (mode == 0 ? sizeof(double) : sizeof(float));
     tr_tree* t = *inout;
-    if (t && (t->N != N || t->mode != mode || t->device != dev)) {
+    if (t && (t->N != N || t->mode != mode || t->device != dev || t->flags)) {
         // the iteration buffers belong to the tree and go with it
         tree_release(t);
         t = nullptr;
@@ -121,6 +129,7 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
         t->device = dev;
         t->N = N; t->L = L; t->mode = mode;
         t->n_nodes = n_nodes;
+        t->n_cells = (int64_t)N * N * N;
         t->nodes_bytes = (size_t)n_nodes * rec;
         if ((rc = dev_alloc(&t->nodes, t->nodes_bytes, "tree nodes")) != TR_OK ||
             (rc = dev_alloc(&t->sums, sum_bytes, "tree build sums")) != TR_OK ||
@@ -146,6 +155,135 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
     if ((rc = table_get(p->nside, &t->table, st)) != TR_OK) return rc;
     if ((rc = sweep_tables_make(&t->sw, nr, p->eta_r, p->nside, t->npix, p->zeta_g ? 1 : 0, st)) != TR_OK) return rc;
     return tree_build(t, g, s, st);
+}
+
+// AMR block layout checks (host): levels and positions in range, no block
+// inside another, and the blocks' volume equal to the box's.
+tr_status check_amr(const tr_amr_grid* g, const tr_sources* s, int* L_out, int* Lb_out) {
+    if (!g) return set_error(TR_EINVAL, "grid is NULL");
+    if (!is_pow2(g->N_base) || g->N_base < 8) return set_error(TR_EINVAL, "N_base must be a power of two >= 8 (got %d)", g->N_base);
+    if (g->max_level < 0 || g->max_level > 6) return set_error(TR_EINVAL, "max_level out of range (got %d)", g->max_level);
+    const int64_t Nf = (int64_t)g->N_base << g->max_level;
+    if (Nf > 512) return set_error(TR_EUNSUPPORTED, "finest lattice N_base << max_level = %lld exceeds 512", (long long)Nf);
+    if (g->n_blocks < 1 || !g->blk_level || !g->blk_pos) return set_error(TR_EINVAL, "no blocks");
+    if (!g->n_H) return set_error(TR_EINVAL, "n_H is NULL");
+    if (!(g->dx_fine > 0.0) || !std::isfinite(g->dx_fine)) return set_error(TR_EINVAL, "dx_fine must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->box_lo[a])) return set_error(TR_EINVAL, "box_lo must be finite");
+    if (s && s->n < 0) return set_error(TR_EINVAL, "negative source count");
+    if (s && s->n > 0 && (!s->xyz || !s->Q)) return set_error(TR_EINVAL, "source arrays are NULL");
+    int L = 0, Lb = 0;
+    while ((1 << L) < Nf) ++L;
+    while ((1 << Lb) < g->N_base) ++Lb;
+    // blocks as nodes of the octree: level Lb - 3 + level, position in blocks
+    std::unordered_set<uint64_t> keys;
+    keys.reserve((size_t)g->n_blocks * 2);
+    auto key = [](int l, int64_t x, int64_t y, int64_t z) {
+        return ((uint64_t)l << 60) | ((uint64_t)z << 40) | ((uint64_t)y << 20) | (uint64_t)x;
+    };
+    unsigned __int128 vol = 0;
+    for (int b = 0; b < g->n_blocks; ++b) {
+        const int lev = g->blk_level[b];
+        if (lev < 0 || lev > g->max_level) return set_error(TR_EINVAL, "block %d: level %d out of range", b, lev);
+        const int64_t nb = (int64_t)(g->N_base >> 3) << lev;
+        for (int a = 0; a < 3; ++a)
+            if (g->blk_pos[3 * b + a] < 0 || g->blk_pos[3 * b + a] >= nb)
+                return set_error(TR_EINVAL, "block %d: position out of range", b);
+        if (!keys.insert(key(lev, g->blk_pos[3 * b], g->blk_pos[3 * b + 1], g->blk_pos[3 * b + 2])).second)
+            return set_error(TR_EINVAL, "block %d repeats another block", b);
+        const int64_t e = (int64_t)1 << (g->max_level - lev);
+        vol += (unsigned __int128)(e * e * e);
+    }
+    for (int b = 0; b < g->n_blocks; ++b) {
+        const int lev = g->blk_level[b];
+        for (int l = lev - 1; l >= 0; --l) {
+            const int sh = lev - l;
+            if (keys.count(key(l, g->blk_pos[3 * b] >> sh, g->blk_pos[3 * b + 1] >> sh, g->blk_pos[3 * b + 2] >> sh)))
+                return set_error(TR_EINVAL, "block %d lies inside a coarser block", b);
+        }
+    }
+    const int64_t nb0 = g->N_base >> 3;
+    const unsigned __int128 e0 = (unsigned __int128)1 << g->max_level;
+    if (vol != (unsigned __int128)(nb0 * nb0 * nb0) * e0 * e0 * e0)
+        return set_error(TR_EINVAL, "the blocks do not fill the box");
+    *L_out = L;
+    *Lb_out = Lb;
+    return TR_OK;
+}
+
+tr_status build_amr(const tr_amr_grid* g, const tr_sources* s, const tr_params* p, tr_tree** inout, cudaStream_t st) {
+    tr_status rc = check_params(p);
+    int L = 0, Lb = 0;
+    if (rc == TR_OK) rc = check_amr(g, s, &L, &Lb);
+    if (rc != TR_OK) return rc;
+    int dev = 0;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice")) != TR_OK) return rc;
+    const int N = g->N_base << g->max_level;
+    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx_fine : (double)N * std::sqrt(3.0);
+    const int nr = p->eta_r * (int)std::floor(std::sqrt(2.0 * lray)) + 1;      // Eq. 5
+    if (nr > MAX_NR) return set_error(TR_EUNSUPPORTED, "N_R = %d exceeds %d evaluation points", nr, MAX_NR);
+    if (nr < 3) return set_error(TR_EINVAL, "L_ray too short: N_R = %d", nr);
+    // host tables: {cell level, x, y, z} per block, and the walk order (the
+    // Morton code of each block's corner on the finest lattice; aligned
+    // cubes are contiguous along the Morton curve)
+    const int nb = g->n_blocks;
+    std::vector<int4> hblk(nb);
+    std::vector<std::pair<uint32_t, uint32_t>> order(nb);
+    for (int b = 0; b < nb; ++b) {
+        const int lev = g->blk_level[b];
+        hblk[b] = make_int4(Lb + lev, g->blk_pos[3 * b], g->blk_pos[3 * b + 1], g->blk_pos[3 * b + 2]);
+        const uint32_t e = 8u << (g->max_level - lev);
+        order[b] = {morton3(g->blk_pos[3 * b] * e, g->blk_pos[3 * b + 1] * e, g->blk_pos[3 * b + 2] * e), (uint32_t)b};
+    }
+    std::sort(order.begin(), order.end());
+    std::vector<uint32_t> horder(nb);
+    for (int b = 0; b < nb; ++b) horder[b] = order[b].second;
+
+    if (*inout) { tree_release(*inout); *inout = nullptr; }
+    const int mode = p->precision;
+    tr_tree* t = new tr_tree();
+    t->device = dev;
+    t->N = N; t->L = L; t->mode = mode;
+    t->n_nodes = level_offset(L + 1);
+    t->n_cells = (int64_t)nb * 512;
+    t->n_blocks = nb;
+    t->nodes_bytes = (size_t)t->n_nodes * (mode == 0 ? sizeof(NodeF64) : sizeof(NodeF32));
+    const size_t sum_bytes = (size_t)t->n_nodes * 3 * (mode == 0 ? sizeof(double) : sizeof(float));
+    if ((rc = dev_alloc(&t->nodes, t->nodes_bytes, "tree nodes")) != TR_OK ||
+        (rc = dev_alloc(&t->sums, sum_bytes, "tree build sums")) != TR_OK ||
+        (rc = dev_alloc(&t->ndot, sizeof(double) * (size_t)t->n_cells, "cell emission")) != TR_OK ||
+        (rc = dev_alloc(&t->status, 4 * sizeof(int32_t), "status words")) != TR_OK ||
+        (rc = dev_alloc(&t->stats, 4 * sizeof(unsigned long long), "walk counters")) != TR_OK ||
+        (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK ||
+        (rc = dev_alloc((unsigned char**)&t->jobbuf, walk_job_bytes(1), "walk job record")) != TR_OK ||
+        (rc = dev_alloc(&t->flags, (size_t)t->n_nodes, "node flags")) != TR_OK ||
+        (rc = dev_alloc(&t->blk, sizeof(int4) * (size_t)nb, "block table")) != TR_OK ||
+        (rc = dev_alloc(&t->blk_order, sizeof(uint32_t) * (size_t)nb, "block order")) != TR_OK ||
+        (rc = dev_alloc(&t->blkmap, sizeof(int32_t) * (size_t)level_offset(L - 2), "block map")) != TR_OK) {
+        tree_release(t);
+        return rc;
+    }
+    t->p = *p;
+    t->use_e = g->e_prev != nullptr;
+    t->nr = nr;
+    t->npix = 12 * p->nside * p->nside;
+    for (int a = 0; a < 3; ++a) t->box_lo[a] = g->box_lo[a];
+    t->dx = g->dx_fine;
+    t->U = p->alpha_B * g->dx_fine * g->dx_fine * g->dx_fine;
+    t->Eu = p->alpha_B * g->dx_fine * p->hnu / C_LIGHT;
+    t->lray = lray;
+    *inout = t;
+    rc = cuda_check(cudaMemcpyAsync(t->blk, hblk.data(), sizeof(int4) * nb, cudaMemcpyHostToDevice, st), "block table copy");
+    if (rc == TR_OK)
+        rc = cuda_check(cudaMemcpyAsync(t->blk_order, horder.data(), sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st),
+                        "block order copy");
+    if (rc == TR_OK) rc = amr_topology(t, st);
+    // the host tables go out of scope on return
+    if (rc == TR_OK) rc = cuda_check(cudaStreamSynchronize(st), "block tables");
+    if (rc != TR_OK) return rc;
+    if ((rc = table_get(p->nside, &t->table, st)) != TR_OK) return rc;
+    if ((rc = sweep_tables_make(&t->sw, nr, p->eta_r, p->nside, t->npix, p->zeta_g ? 1 : 0, st)) != TR_OK) return rc;
+    return tree_build_amr(t, g->n_H, g->ndot, g->e_prev, s, st);
 }
 
 std::mutex g_solve_mu;
@@ -217,6 +355,20 @@ void tr_params_default(tr_params* p) {
 
 const char* tr_last_error(void) { return g_err; }
 
+tr_status tr_build_tree_amr(const tr_amr_grid* g, const tr_sources* s, const tr_params* p, tr_tree** out,
+                            tr_stream stream) {
+    g_err[0] = '\0';
+    if (!out) return set_error(TR_EINVAL, "out is NULL");
+    return build_amr(g, s, p, out, (cudaStream_t)stream);
+}
+
+tr_status tr_tree_cells(const tr_tree* t, int64_t* n_cells) {
+    g_err[0] = '\0';
+    if (!t || !n_cells) return set_error(TR_EINVAL, "tree or output is NULL");
+    *n_cells = t->n_cells;
+    return TR_OK;
+}
+
 tr_status tr_build_tree(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tree** out, tr_stream stream) {
     g_err[0] = '\0';
     if (!out) return set_error(TR_EINVAL, "out is NULL");
@@ -227,9 +379,9 @@ tr_status tr_walk_map(const tr_tree* t, const int64_t* targets, int64_t n_target
     g_err[0] = '\0';
     cudaStream_t st = (cudaStream_t)stream;
     if (!t || !out) return set_error(TR_EINVAL, "tree or out is NULL");
-    const int64_t ncell = (int64_t)t->N * t->N * t->N;
+    const int64_t ncell = t->n_cells;
     if (n_targets < 0 || n_targets > ncell) return set_error(TR_EINVAL, "n_targets out of range");
-    if (!targets && n_targets != ncell) return set_error(TR_EINVAL, "targets NULL requires n_targets = N^3");
+    if (!targets && n_targets != ncell) return set_error(TR_EINVAL, "targets NULL requires n_targets = the cell count");
     tr_rays* r = new tr_rays();
     r->device = t->device;
     r->n_targets = n_targets;
@@ -277,7 +429,7 @@ tr_status tr_walk_sweep(const tr_tree* t, double* F_out, double* e_out, uint8_t*
     if (!t) return set_error(TR_EINVAL, "tree is NULL");
     WalkOut o;
     o.F = F_out; o.e = e_out; o.ion = ion_out;
-    tr_status rc = walk_run(t, nullptr, (int64_t)t->N * t->N * t->N, false, o, st);
+    tr_status rc = walk_run(t, nullptr, t->n_cells, false, o, st);
     if (rc == TR_OK) rc = read_status(t, st);
     return rc;
 }
@@ -305,9 +457,8 @@ tr_status tr_walk_sweep_batch(const tr_tree* const* trees, const int64_t* first,
         if (!t) return set_error(TR_EINVAL, "tree %d is NULL", i);
         if (t->device != dev) return set_error(TR_EINVAL, "tree %d lives on device %d, current is %d", i, t->device, dev);
         if (t->mode != trees[0]->mode) return set_error(TR_EINVAL, "trees of one batch share a precision");
-        const int64_t ncell = (int64_t)t->N * t->N * t->N;
-        if (first[i] < 0 || count[i] < 0 || first[i] + count[i] > ncell)
-            return set_error(TR_EINVAL, "target range %d out of [0, N^3)", i);
+        if (first[i] < 0 || count[i] < 0 || first[i] + count[i] > t->n_cells)
+            return set_error(TR_EINVAL, "target range %d out of [0, cells)", i);
     }
     std::lock_guard<std::mutex> lock(g_batch_mu);
     BatchSpace& b = g_batch[dev];
@@ -421,6 +572,12 @@ tr_status tr_tree_info(const tr_tree* t, int64_t* n_nodes, int32_t* levels, int3
     if (nr) *nr = t->nr;
     if (npix) *npix = t->npix;
     return TR_OK;
+}
+
+tr_status tr_tree_flags(const tr_tree* t, uint8_t* out, tr_stream stream) {
+    g_err[0] = '\0';
+    if (!t || !out) return set_error(TR_EINVAL, "tree or output is NULL");
+    return flags_export(t, out, (cudaStream_t)stream);
 }
 
 tr_status tr_tree_nodes(const tr_tree* t, double* out8, tr_stream stream) {

@@ -28,6 +28,10 @@ constexpr int MAX_NR = 128;
 constexpr double PI_D = 3.14159265358979323846;
 constexpr double DELTA_IF = 1e-8;           // Sec. 2.4
 
+// node topology of an AMR tree (one byte per node; uniform trees need none:
+// a node is a leaf exactly when it is on the finest level)
+constexpr uint8_t NODE_ABSENT = 0, NODE_LEAF = 1, NODE_PARENT = 2;
+
 struct NodeF64 { double cmx, cmy, cmz, m, alpha, eps, e, mion; };   // 64 B
 struct NodeF32 { float cmx, cmy, cmz, m, alpha, eps, e, mion; };    // 32 B
 
@@ -100,6 +104,13 @@ struct tr_tree {
     void* jobbuf = nullptr;                 // device copy of the walk's job record
     double* e_work = nullptr;               // tr_solve iteration: 2 x N^3 energy densities
     void* dscratch = nullptr;               // tr_solve iteration: delta reduction state
+    int64_t n_cells = 0;                    // targets: N^3, or n_blocks x 512 (AMR)
+    // AMR trees only (NULL / 0 for a uniform grid)
+    int32_t n_blocks = 0;
+    uint8_t* flags = nullptr;               // n_nodes: NODE_ABSENT / NODE_LEAF / NODE_PARENT
+    int4* blk = nullptr;                    // n_blocks: {tree level of its cells, x, y, z position in blocks}
+    uint32_t* blk_order = nullptr;          // n_blocks: blocks along the Morton curve of the finest lattice
+    int32_t* blkmap = nullptr;              // nodes of levels 0 .. L-3: block index, or -1
 };
 
 struct tr_rays {
@@ -131,7 +142,14 @@ tr_status table_build_into(int nside, Table* t, uint32_t* counts, uint32_t ent_c
 
 // tree (tr_tree.cu)
 tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStream_t st);
+// AMR: t->flags, blk, blk_order, blkmap are set up (device) and t->n_cells
+// = n_blocks x 512; n_H, ndot, e_prev are cell arrays in block order
+tr_status tree_build_amr(tr_tree* t, const double* n_H, const double* ndot, const double* e_prev,
+                         const tr_sources* s, cudaStream_t st);
+// AMR: flags and block map from t->blk (once per block layout)
+tr_status amr_topology(tr_tree* t, cudaStream_t st);
 tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st);
+tr_status flags_export(const tr_tree* t, uint8_t* out, cudaStream_t st);
 tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g,
                             cudaStream_t st);
 void sweep_tables_free(SweepTables* sw);

@@ -147,6 +147,7 @@ extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, con
     t.device = dev;
     t.N = N; t.L = L; t.mode = p->precision;
     t.n_nodes = level_offset(L + 1);
+    t.n_cells = NA_NCELL < (int64_t)N * N * N ? NA_NCELL : (int64_t)N * N * N;
     t.nodes = ds.base + OFF_NODES;
     t.sums = ds.base + OFF_SUMS;
     t.ndot = at<double>(ds.base, OFF_NDOT);

@@ -86,13 +86,117 @@ __global__ void k_leaves(void* nodes_v, void* sums_v, int N, int L, const double
     }
 }
 
-// One level of parents from their eight contiguous children.
+// ---- AMR grids: blocks of 8^3 cells, cells of edge N >> level ------------
+
+// Topology: every cell of a block is a leaf; the 64 + 8 + 1 nodes above the
+// cells inside the block and every ancestor of the block are parents (many
+// blocks store the same byte into a shared ancestor).  The block's own node
+// also records the block index, so a cell can be found from its position.
+__global__ void k_amr_topology(uint8_t* flags, int32_t* blkmap, const int4* blk, int n_blocks) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_blocks * 512) return;
+    const int b = (int)(i >> 9), c = (int)(i & 511);
+    const int4 bm = blk[b];
+    const int tl = bm.x;
+    const uint32_t bx = (uint32_t)bm.y, by = (uint32_t)bm.z, bz = (uint32_t)bm.w;
+    flags[level_offset(tl) + morton3(8 * bx + (c & 7), 8 * by + ((c >> 3) & 7), 8 * bz + (c >> 6))] = NODE_LEAF;
+    if (c < 64) {
+        flags[level_offset(tl - 1) + morton3(4 * bx + (c & 3), 4 * by + ((c >> 2) & 3), 4 * bz + (c >> 4))] = NODE_PARENT;
+    } else if (c < 72) {
+        const int k = c - 64;
+        flags[level_offset(tl - 2) + morton3(2 * bx + (k & 1), 2 * by + ((k >> 1) & 1), 2 * bz + (k >> 2))] = NODE_PARENT;
+    } else if (c == 72) {
+        const int64_t id = level_offset(tl - 3) + morton3(bx, by, bz);
+        flags[id] = NODE_PARENT;
+        blkmap[id] = b;
+    } else if (c - 73 < tl - 3) {
+        const int l = tl - 4 - (c - 73), sh = tl - 3 - l;
+        flags[level_offset(l) + morton3(bx >> sh, by >> sh, bz >> sh)] = NODE_PARENT;
+    }
+}
+
+// Point sources go to the cell containing their finest-lattice cell: the
+// first leaf on the way down from the root.
+__global__ void k_amr_map_sources(double* ndot, const uint8_t* flags, const int32_t* blkmap, int N, int L,
+                                  double lo0, double lo1, double lo2, double dx, const double* xyz, const double* Q,
+                                  int n) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double lo[3] = {lo0, lo1, lo2};
+    uint32_t f[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = floor(__ddiv_rn(__dsub_rn(xyz[3 * s + a], lo[a]), dx));
+        v = fmin(fmax(v, 0.0), (double)(N - 1));
+        f[a] = (uint32_t)v;
+    }
+    for (int l = 3; l <= L; ++l) {                   // a cell lies at level >= 3 (N_base >= 8)
+        const int sh = L - l;
+        const uint32_t x = f[0] >> sh, y = f[1] >> sh, z = f[2] >> sh;
+        if (flags[level_offset(l) + morton3(x, y, z)] == NODE_LEAF) {
+            const int b = blkmap[level_offset(l - 3) + morton3(x >> 3, y >> 3, z >> 3)];
+            const int64_t cell = ((int64_t)b << 9) + (int64_t)(((z & 7) * 8 + (y & 7)) * 8 + (x & 7));
+            atomicAdd(&ndot[cell], Q[s]);
+            return;
+        }
+    }
+}
+
+// AMR cells: Eq. 1-3 for a cell of edge s (volume s^3 finest cells), stored
+// at its own level of the finest-lattice octree.
 template <int MODE>
-__global__ void k_parents(void* nodes_v, void* sums_v, int l, int N) {
+__global__ void k_amr_leaves(void* nodes_v, void* sums_v, int N, const int4* blk, int n_blocks, const double* n_H,
+                             const double* ndot, const double* e_prev, double invU, double invEu) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_blocks * 512) return;
+    const int b = (int)(i >> 9), c = (int)(i & 511);
+    const int4 bm = blk[b];
+    const int tl = bm.x;
+    const uint32_t ix = 8 * (uint32_t)bm.y + (c & 7), iy = 8 * (uint32_t)bm.z + ((c >> 3) & 7),
+                   iz = 8 * (uint32_t)bm.w + (c >> 6);
+    const int64_t id = level_offset(tl) + morton3(ix, iy, iz);
+    const double s = (double)(N >> tl), vol = s * s * s;
+    const double n = n_H[i];
+    const double rec = n * n * vol;                  // alpha_B n^2 dV in units of U
+    const double src = ndot[i] * invU;
+    const double ep = e_prev ? e_prev[i] : 0.0;
+    const double px = ((double)ix + 0.5) * s, py = ((double)iy + 0.5) * s, pz = ((double)iz + 0.5) * s;
+    if (MODE == 0) {
+        NodeF64 nd;
+        nd.m = __dmul_rn(n, vol);
+        const double sx = __dmul_rn(nd.m, px), sy = __dmul_rn(nd.m, py), sz = __dmul_rn(nd.m, pz);
+        if (nd.m > 0.0) { nd.cmx = __ddiv_rn(sx, nd.m); nd.cmy = __ddiv_rn(sy, nd.m); nd.cmz = __ddiv_rn(sz, nd.m); }
+        else { nd.cmx = px; nd.cmy = py; nd.cmz = pz; }
+        nd.alpha = fmax(rec - src, 0.0);
+        nd.eps = fmax(src - rec, 0.0);
+        nd.e = ep * invEu * vol;
+        nd.mion = (ep > 0.0) ? nd.m : 0.0;
+        ((NodeF64*)nodes_v)[id] = nd;
+        double* sm = (double*)sums_v + 3 * id;
+        sm[0] = sx; sm[1] = sy; sm[2] = sz;
+    } else {
+        NodeF32 nd;
+        const float mf = (float)(n * vol);
+        nd.m = mf;
+        nd.cmx = (float)px; nd.cmy = (float)py; nd.cmz = (float)pz;
+        nd.alpha = (float)fmax(rec - src, 0.0);
+        nd.eps = (float)fmax(src - rec, 0.0);
+        nd.e = (float)(ep * invEu * vol);
+        nd.mion = (ep > 0.0) ? mf : 0.f;
+        ((NodeF32*)nodes_v)[id] = nd;
+        float* sm = (float*)sums_v + 3 * id;
+        sm[0] = mf * nd.cmx; sm[1] = mf * nd.cmy; sm[2] = mf * nd.cmz;
+    }
+}
+
+// One level of parents from their eight contiguous children (on an AMR
+// tree only the nodes flagged as parents).
+template <int MODE>
+__global__ void k_parents(void* nodes_v, void* sums_v, int l, int N, const uint8_t* flags) {
     const int64_t nl = int64_t(1) << (3 * l);
     int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (m >= nl) return;
     const int64_t id = level_offset(l) + m;
+    if (flags && flags[id] != NODE_PARENT) return;
     const int64_t ch = level_offset(l + 1) + 8 * m;
     const uint32_t ix = compact3((uint32_t)m), iy = compact3((uint32_t)m >> 1), iz = compact3((uint32_t)m >> 2);
     const double s = (double)(N >> l);
@@ -198,6 +302,11 @@ __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g,
 
 inline unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+__global__ void k_uniform_flags(uint8_t* out, int64_t n, int64_t first_leaf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = i >= first_leaf ? NODE_LEAF : NODE_PARENT;
+}
+
 }  // namespace
 
 tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g,
@@ -262,10 +371,52 @@ tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStre
                                                          g->e_prev, invU, invEu);
     for (int l = t->L - 1; l >= 0; --l) {
         const int64_t nl = int64_t(1) << (3 * l);
-        if (t->mode == 0) k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N);
-        else k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N);
+        if (t->mode == 0) k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, nullptr);
+        else k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, nullptr);
     }
     return cuda_check(cudaGetLastError(), "tree build kernels");
+}
+
+tr_status amr_topology(tr_tree* t, cudaStream_t st) {
+    tr_status rc = cuda_check(cudaMemsetAsync(t->flags, 0, (size_t)t->n_nodes, st), "clear flags");
+    if (rc == TR_OK)
+        rc = cuda_check(cudaMemsetAsync(t->blkmap, 0xff, sizeof(int32_t) * (size_t)level_offset(t->L - 2), st),
+                        "clear block map");
+    if (rc != TR_OK) return rc;
+    k_amr_topology<<<grid_for(t->n_cells, 256), 256, 0, st>>>(t->flags, t->blkmap, t->blk, t->n_blocks);
+    return cuda_check(cudaGetLastError(), "topology kernel");
+}
+
+tr_status tree_build_amr(tr_tree* t, const double* n_H, const double* ndot, const double* e_prev,
+                         const tr_sources* s, cudaStream_t st) {
+    const int64_t ncell = t->n_cells;
+    const double invU = 1.0 / t->U, invEu = 1.0 / t->Eu;
+    // nodes inside a cell are never written by the build: keep them zero
+    tr_status rc = cuda_check(cudaMemsetAsync(t->nodes, 0, t->nodes_bytes, st), "clear nodes");
+    if (rc != TR_OK) return rc;
+    k_ndot_init<<<grid_for(ncell, 256), 256, 0, st>>>(t->ndot, ndot, ncell);
+    if (s && s->n > 0)
+        k_amr_map_sources<<<grid_for(s->n, 128), 128, 0, st>>>(t->ndot, t->flags, t->blkmap, t->N, t->L, t->box_lo[0],
+                                                               t->box_lo[1], t->box_lo[2], t->dx, s->xyz, s->Q, s->n);
+    if (t->mode == 0)
+        k_amr_leaves<0><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->blk, t->n_blocks, n_H,
+                                                             t->ndot, e_prev, invU, invEu);
+    else
+        k_amr_leaves<1><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->blk, t->n_blocks, n_H,
+                                                             t->ndot, e_prev, invU, invEu);
+    for (int l = t->L - 1; l >= 0; --l) {
+        const int64_t nl = int64_t(1) << (3 * l);
+        if (t->mode == 0) k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, t->flags);
+        else k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, t->flags);
+    }
+    return cuda_check(cudaGetLastError(), "AMR tree build kernels");
+}
+
+tr_status flags_export(const tr_tree* t, uint8_t* out, cudaStream_t st) {
+    if (t->flags)
+        return cuda_check(cudaMemcpyAsync(out, t->flags, (size_t)t->n_nodes, cudaMemcpyDeviceToDevice, st), "flags copy");
+    k_uniform_flags<<<grid_for(t->n_nodes, 256), 256, 0, st>>>(out, t->n_nodes, level_offset(t->L));
+    return cuda_check(cudaGetLastError(), "flags kernel");
 }
 
 tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st) {

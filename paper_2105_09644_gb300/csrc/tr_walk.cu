@@ -50,8 +50,12 @@ struct WalkArgs {
     const float* Gf;
     const float* ID2f;
     const float* GIf;
-    const int64_t* targets;                 // NULL: cells first .. first+n_targets-1 in Morton order
+    const int64_t* targets;                 // NULL: cells first .. first+n_targets-1 in walk order
     int64_t first;
+    const uint8_t* flags;                   // AMR tree: node topology (NULL: uniform grid)
+    const int4* blk;                        // AMR tree: per block {cell level, x, y, z}
+    const uint32_t* blk_order;              // AMR tree: blocks in walk order
+    int64_t n_cells;                        // valid target indices are [0, n_cells)
     int64_t n_targets;
     double Fconv, Econv;                    // scaled flux -> CGS flux / energy density
     double* F;
@@ -654,9 +658,36 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             }
         }
         const int64_t q = qg - (j > 0 ? job_end[j - 1] : 0);    // index within the job
-        int tx, ty, tz;
+        if (a.targets) {                                         // caller's list: reject bad indices
+            const int64_t c = a.targets[q];
+            if (c < 0 || c >= a.n_cells) {                       // (uniform over the CTA)
+                if (tid == 0) atomicAdd(a.status + 2, 1);
+                __syncthreads();                                 // s_q, s_j read before thread 0 rewrites them
+                continue;
+            }
+        }
+        int tx, ty, tz;                                          // target corner (finest cells)
+        int ts = 1, tl = L;                                      // its edge and level
         int64_t cell;
-        if (a.targets) {
+        if (a.blk) {                                             // AMR: cell c of block b
+            int b, lx, ly, lz;
+            if (a.targets) {
+                cell = a.targets[q];
+                b = (int)(cell >> 9);
+                const int c = (int)(cell & 511);
+                lx = c & 7; ly = (c >> 3) & 7; lz = c >> 6;
+            } else {
+                const int64_t k = a.first + q;
+                b = (int)__ldg(a.blk_order + (k >> 9));
+                const uint32_t lm = (uint32_t)(k & 511);
+                lx = (int)compact3(lm); ly = (int)compact3(lm >> 1); lz = (int)compact3(lm >> 2);
+                cell = ((int64_t)b << 9) + (lz * 8 + ly) * 8 + lx;
+            }
+            const int4 bm = __ldg(a.blk + b);
+            tl = bm.x;
+            ts = N >> tl;
+            tx = (8 * bm.y + lx) * ts; ty = (8 * bm.z + ly) * ts; tz = (8 * bm.w + lz) * ts;
+        } else if (a.targets) {
             cell = a.targets[q];
             tx = (int)(cell % N); ty = (int)((cell / N) % N); tz = (int)(cell / ((int64_t)N * N));
         } else {
@@ -664,7 +695,8 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             tx = (int)compact3(m); ty = (int)compact3(m >> 1); tz = (int)compact3(m >> 2);
             cell = ((int64_t)tz * N + ty) * N + tx;
         }
-        const real px = (real)tx + real(0.5), py = (real)ty + real(0.5), pz = (real)tz + real(0.5);
+        const real hts = real(0.5) * (real)ts;
+        const real px = (real)tx + hts, py = (real)ty + hts, pz = (real)tz + hts;
         for (int b = tid; b < nq * nbins; b += NT) bins_a[b] = 0.0;
         if (tid == 0) { stack[0] = 0u; s_nacc = 0; }               // the root, opened
         int top = 1, max_top = 1;
@@ -690,14 +722,16 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                           cz = (int)compact3(mort >> 2) * s;
                 const bool contains = (tx >= cx && tx < cx + s) && (ty >= cy && ty < cy + s) &&
                                       (tz >= cz && tz < cz + s);
+                const int64_t nid = level_offset(lev) + mort;
+                const bool leaf = a.flags ? (__ldg(a.flags + nid) == NODE_LEAF) : (lev == L);
                 if (contains) {
-                    action = (lev == L) ? 0 : 1;
+                    action = leaf ? 0 : 1;                       // a leaf holding the target is the target
                 } else {
                     real cm[3], m, qv[3], mion;
-                    load_node<MODE>(a.nodes, level_offset(lev) + mort, cm, m, qv, mion);
+                    load_node<MODE>(a.nodes, nid, cm, m, qv, mion);
                     const real d2 = dist2(px, py, pz, cm);
                     const real h2 = (real)s * (real)s;
-                    if (lev < L && must_open(h2, d2, m, mion, qv[1], a)) {
+                    if (!leaf && must_open(h2, d2, m, mion, qv[1], a)) {
                         action = 1;
                     } else {
                         action = 2;
@@ -705,8 +739,8 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                         const bool in_reach = (MODE == 0) ? ((double)d <= a.lray) : ((float)d <= a.lrayf);
                         const bool has_ae = qv[0] != real(0) || (a.use_e && qv[2] != real(0));
                         if (in_reach && (has_ae || qv[1] != real(0))) {
-                            const int key = table_key(2 * cx + s - 2 * tx - 1, 2 * cy + s - 2 * ty - 1,
-                                                      2 * cz + s - 2 * tz - 1, s);
+                            const int key = table_key(2 * cx + s - 2 * tx - ts, 2 * cy + s - 2 * ty - ts,
+                                                      2 * cz + s - 2 * tz - ts, s);
                             const uint2 hd = __ldg(a.hdr + key);
                             ne = (int)hd.y;
                             n_ent += ne;
@@ -791,9 +825,11 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             max_top = max(max_top, top);
         }
         __syncthreads();                                         // all spreads done
-        // own emission of the target (Sec. 2.5 footnote: target sphere r_tp = dx/2)
+        // own emission of the target (Sec. 2.5 footnote: target sphere of
+        // radius r_tp = half the cell edge)
         real cmt[3], mt, qt[3], miont;
-        load_node<MODE>(a.nodes, level_offset(L) + morton3(tx, ty, tz), cmt, mt, qt, miont);
+        load_node<MODE>(a.nodes, level_offset(tl) + morton3(tx / ts, ty / ts, tz / ts), cmt, mt, qt, miont);
+        const double r_tp2 = 0.25 * (double)ts * (double)ts;
         const double eps_self = (double)qt[1];
         if (tid == 0) atomicMax(a.status + 1, max_top);
         if (overflow) {
@@ -812,13 +848,13 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             }
             if (tid == 0) {
                 a.counts_out[q] = s_nacc;
-                a.eps_self_out[q] = eps_self;
+                a.eps_self_out[q] = eps_self / ((double)ts * (double)ts);   // reaches the centre as for ts = 1
                 if (q == 0) { a.scales_out[0] = sc.a; a.scales_out[1] = sc.eps; a.scales_out[2] = sc.e; }
             }
             continue;
         }
         const double Fk = sweep_rays<MODE, NT>(a, bins_a, bins_eps, bins_e, sc);
-        const double F = block_sum<NT>(Fk, s_red) + eps_self / (4.0 * PI_D * 0.25);
+        const double F = block_sum<NT>(Fk, s_red) + eps_self / (4.0 * PI_D * r_tp2);
         if (tid == 0) {
             const int64_t o = a.targets ? q : cell;
             if (a.F) a.F[o] = F * a.Fconv;
@@ -890,12 +926,29 @@ WalkArgs make_args(const tr_tree* t) {
     a.Econv = t->Eu;
     a.status = t->status;
     a.stats = t->stats;
+    a.n_cells = t->n_cells;
+    a.flags = t->flags;
+    a.blk = t->blk;
+    a.blk_order = t->blk_order;
     return a;
 }
 
 template <typename K>
 tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
                             int64_t total, unsigned int* counter, cudaStream_t st) {
+    {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        cudaGetDevice(&dev);
+        tr_status c = cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+                                 "shared memory limit");
+        if (c == TR_OK) c = cuda_check(cudaFuncGetAttributes(&fa, kernel), "kernel attributes");
+        if (c != TR_OK) return c;
+        if (smem + fa.sharedSizeBytes > (size_t)optin)
+            return set_error(TR_EUNSUPPORTED,
+                             "ray bins need %zu + %zu bytes of shared memory per target, more than the %d a CTA can have"
+                             " (fewer rays, a shorter L_ray or no e_prev)", smem, (size_t)fa.sharedSizeBytes, optin);
+    }
     tr_status s = cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "cudaFuncSetAttribute(smem)");
     if (s != TR_OK) return s;
@@ -1008,6 +1061,7 @@ tr_status read_status(const tr_tree* t, cudaStream_t st) {
     tr_status s = cuda_check(cudaMemcpyAsync(h, t->status, sizeof h, cudaMemcpyDeviceToHost, st), "status copy");
     if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "walk kernels");
     if (s != TR_OK) return s;
+    if (h[2] > 0) return set_error(TR_EINVAL, "%d target index(es) outside [0, %lld)", h[2], (long long)t->n_cells);
     if (h[0] > 0)
         return set_error(TR_EOVERFLOW, "the walk stack overflowed for %d target(s); their outputs are NaN", h[0]);
     return TR_OK;

@@ -47,3 +47,31 @@ def amr_cells(g):
     corner = (8 * g.blk_pos.astype(np.int64)[:, None, :] + local[None, :, :]) * size[:, None, None]
     return corner.reshape(-1, 3), np.repeat(size, 512)
 
+
+
+def amr_paint(g, values):
+    """Cell values of an AMR grid painted onto its finest lattice [z, y, x]."""
+    N = g.N_fine
+    out = np.empty((N, N, N), dtype=np.asarray(values).dtype)
+    v = np.asarray(values).reshape(g.n_blocks, 8, 8, 8)
+    for b in range(g.n_blocks):
+        s = g.cell_size(b)
+        x0, y0, z0 = 8 * s * g.blk_pos[b]
+        blk = np.repeat(np.repeat(np.repeat(v[b], s, 0), s, 1), s, 2)
+        out[z0:z0 + 8 * s, y0:y0 + 8 * s, x0:x0 + 8 * s] = blk
+    return out
+
+
+def amr_interior_mask(g, ion):
+    """AMR cells whose neighbourhood (the cell grown by one finest cell on
+    every side) holds one ionised/neutral class: cells not at a front."""
+    from scipy import ndimage
+    fine = amr_paint(g, np.asarray(ion).astype(np.int8))
+    uniform = ndimage.minimum_filter(fine, size=3, mode="nearest") == ndimage.maximum_filter(fine, size=3, mode="nearest")
+    out = np.empty((g.n_blocks, 8, 8, 8), dtype=bool)
+    for b in range(g.n_blocks):
+        s = g.cell_size(b)
+        x0, y0, z0 = 8 * s * g.blk_pos[b]
+        sub = uniform[z0:z0 + 8 * s, y0:y0 + 8 * s, x0:x0 + 8 * s]
+        out[b] = sub.reshape(8, s, 8, s, 8, s).all(axis=(1, 3, 5))
+    return out.ravel()
