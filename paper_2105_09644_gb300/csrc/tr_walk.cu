@@ -896,6 +896,12 @@ __global__ void __launch_bounds__(NT) k_sweep_stored(WalkArgs a, const double* b
 }
 
 constexpr int WALK_NT = 128;                // threads per target (one CTA)
+// Wide CTAs for targets whose ray bins leave room for fewer than three
+// 128-thread CTAs on an SM (N_PIX = 192 with N_R ~ 60 fills most of it):
+// one CTA per SM then brings 16 (FP32 form) or 8 (FP64) warps instead of 4.
+// The FP64 form keeps NT * 12 W_p values in shared memory, hence 256.
+constexpr int WALK_NT_WIDE_F32 = 512;
+constexpr int WALK_NT_WIDE_F64 = 256;
 
 // Opened nodes waiting on a target's stack.  The stack never holds more
 // than the target's opened nodes (a few hundred at theta = 0.5); overflow
@@ -933,7 +939,7 @@ WalkArgs make_args(const tr_tree* t) {
     return a;
 }
 
-template <typename K>
+template <int NT, typename K>
 tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
                             int64_t total, unsigned int* counter, cudaStream_t st) {
     {
@@ -955,24 +961,44 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const i
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, WALK_NT, smem), "occupancy query");
+    s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem), "occupancy query");
     if (s != TR_OK) return s;
     if (per_sm < 1) return set_error(TR_EUNSUPPORTED, "ray bins need %zu bytes of shared memory per target", smem);
     s = cuda_check(cudaMemsetAsync(counter, 0, sizeof(unsigned int), st), "counter reset");
     if (s != TR_OK) return s;
     int64_t blocks = (int64_t)sms * per_sm;
     if (blocks > total) blocks = total > 0 ? total : 1;
-    kernel<<<(unsigned)blocks, WALK_NT, smem, st>>>(jobs, job_end, n_jobs, counter);
+    kernel<<<(unsigned)blocks, NT, smem, st>>>(jobs, job_end, n_jobs, counter);
     return cuda_check(cudaGetLastError(), "walk kernel launch");
+}
+
+bool wide_ctas(int mode, size_t smem) {
+    int per_sm = 0;
+    const void* k = mode == 0 ? (const void*)k_walk<0, false, WALK_NT> : (const void*)k_walk<1, false, WALK_NT>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WALK_NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return true;                                             // too large for 128 threads: try wide
+    }
+    return per_sm < 3;
 }
 
 tr_status launch_jobs(int mode, bool dump, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
                       int64_t total, unsigned int* counter, cudaStream_t st) {
+    constexpr int W0 = WALK_NT_WIDE_F64, W1 = WALK_NT_WIDE_F32;
+    if (wide_ctas(mode, smem)) {
+        if (mode == 0)
+            return dump ? launch_persistent<W0>(k_walk<0, true, W0>, smem, jobs, job_end, n_jobs, total, counter, st)
+                        : launch_persistent<W0>(k_walk<0, false, W0>, smem, jobs, job_end, n_jobs, total, counter, st);
+        return dump ? launch_persistent<W1>(k_walk<1, true, W1>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent<W1>(k_walk<1, false, W1>, smem, jobs, job_end, n_jobs, total, counter, st);
+    }
+    constexpr int T = WALK_NT;
     if (mode == 0)
-        return dump ? launch_persistent(k_walk<0, true, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent(k_walk<0, false, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st);
-    return dump ? launch_persistent(k_walk<1, true, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st)
-                : launch_persistent(k_walk<1, false, WALK_NT>, smem, jobs, job_end, n_jobs, total, counter, st);
+        return dump ? launch_persistent<T>(k_walk<0, true, T>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent<T>(k_walk<0, false, T>, smem, jobs, job_end, n_jobs, total, counter, st);
+    return dump ? launch_persistent<T>(k_walk<1, true, T>, smem, jobs, job_end, n_jobs, total, counter, st)
+                : launch_persistent<T>(k_walk<1, false, T>, smem, jobs, job_end, n_jobs, total, counter, st);
 }
 
 }  // namespace

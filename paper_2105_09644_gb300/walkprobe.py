@@ -1,6 +1,7 @@
 """Run the fused walk kernel on a named workload, for profiling.
 
 python -m paper_2105_09644_gb300.walkprobe --workload turbulent64 --precision 1 --reps 2
+python -m paper_2105_09644_gb300.walkprobe --workload amr_cluster --precision 1 --reps 2
 
 Builds the tree once, then runs tr_walk_sweep `reps` times and prints the
 walk counters and the mean time per launch (CUDA events).
@@ -25,16 +26,27 @@ def main(argv=None):
     from paper_2105_09644_gb300 import binding as B
     from workloads import workload
     B.load()
-    w = workload(a.workload)
-    n = torch.from_numpy(w.n_H).cuda()
+    if a.workload.startswith("amr"):
+        from workloads.amr import amr_cluster
+        w = amr_cluster()
+        n = torch.from_numpy(w.n_H.ravel()).cuda()
+        grid = B.make_amr_grid(w.N_base, w.max_level, w.blk_level, w.blk_pos, n, w.dx_fine)
+        build = B.tr_build_tree_amr
+        shape = (w.n_leaves,)
+    else:
+        w = workload(a.workload)
+        n = torch.from_numpy(w.n_H).cuda()
+        grid = B.make_grid(n, w.dx)
+        build = B.tr_build_tree
+        shape = (w.N,) * 3
     x = torch.from_numpy(w.src_xyz).cuda()
     q = torch.from_numpy(w.src_Q).cuda()
-    tree = B.tr_build_tree(B.make_grid(n, w.dx), B.make_sources(x, q),
-                           B.tr_params_default(nside=w.nside, theta_lim=w.theta_lim, theta_src=w.theta_src,
-                                               precision=a.precision))
-    F = torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda")
+    tree = build(grid, B.make_sources(x, q),
+                 B.tr_params_default(nside=w.nside, theta_lim=w.theta_lim, theta_if=w.theta_if,
+                                     theta_src=w.theta_src, precision=a.precision))
+    F = torch.empty(shape, dtype=torch.float64, device="cuda")
     E = torch.empty_like(F)
-    ion = torch.empty((w.N,) * 3, dtype=torch.uint8, device="cuda")
+    ion = torch.empty(shape, dtype=torch.uint8, device="cuda")
     ms = []
     for _ in range(a.reps):
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
