@@ -49,10 +49,25 @@ typedef enum {
                                (Kahan-Neumaier) sums; FP64 sweep and classification */
 } tr_precision;
 
+/* Radial kernels (App. A) that spread a node along a ray.  alpha and e use
+ * W_p (default) or the truncated Gaussian W_g, normalised over the
+ * evaluation points.  eps uses one of the flux-conserving kernels (W_f,3 by
+ * default, two points with the sum and the flux at the target exact; W_f,1
+ * and W_f,2 with the paper's other second conditions; the generalised
+ * W_f,3 over every point in the node's support, Eq. A8-A10) or, for
+ * comparison, W_p or W_g.  Where a flux kernel's prescription does not
+ * apply (W_f,2 next to the target, a generalised W_f,3 with fewer than three
+ * points or a negative weight) the two-point W_f,3 is used. */
+typedef enum { TR_KERNEL_WP = 0, TR_KERNEL_WG = 1 } tr_kernel;
+typedef enum {
+    TR_EPS_WF3 = 0, TR_EPS_WF1 = 1, TR_EPS_WF2 = 2, TR_EPS_WF3N = 3, TR_EPS_WP = 4, TR_EPS_WG = 5
+} tr_eps_kernel;
+
 /* Solver parameters (Sec. 2.2-2.6).  tr_params_default() fills the paper's
  * defaults: theta_lim 0.5, theta_if = theta_src = INFINITY, N_side 2,
  * eta_R 2, L_ray = domain diagonal, alpha_B 2.7e-13, h nu = 13.6 eV,
- * eps_lim 1e-2, delta per cell, one pass, FP64, zeta_g on. */
+ * eps_lim 1e-2, delta per cell, one pass, FP64, zeta_g on, W_p for alpha
+ * and e, W_f,3 for eps. */
 typedef struct {
     double theta_lim;       /* BH opening angle: accept when h/d < theta_lim (Sec. 2.4) */
     double theta_if;        /* IF MAC angle, INFINITY disables (Sec. 2.4) */
@@ -67,6 +82,8 @@ typedef struct {
     int32_t max_iter;       /* >= 1 passes of build + walk + sweep */
     int32_t precision;      /* tr_precision */
     int32_t zeta_g;         /* 1: apply the geometric factor zeta_g (Eq. 16) */
+    int32_t kernel_alpha;   /* tr_kernel for alpha and e */
+    int32_t kernel_eps;     /* tr_eps_kernel for eps */
 } tr_params;
 
 /* Uniform cubic grid.  N is a power of two with 8 <= N <= 512.

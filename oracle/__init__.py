@@ -43,7 +43,13 @@ class Params(C.Structure):
     _fields_ = [("N", C.c_int32), ("dx_cm", C.c_double), ("nside", C.c_int32),
                 ("eta_r", C.c_int32), ("theta_lim", C.c_double), ("theta_if", C.c_double),
                 ("theta_src", C.c_double), ("lray_cells", C.c_double),
-                ("alpha_B", C.c_double), ("hnu", C.c_double), ("zeta_g", C.c_int32)]
+                ("alpha_B", C.c_double), ("hnu", C.c_double), ("zeta_g", C.c_int32),
+                ("kernel_alpha", C.c_int32), ("kernel_eps", C.c_int32)]
+
+
+# kernel choices (App. A): kernel_alpha for alpha and e, kernel_eps for eps
+K_WP, K_WG = 0, 1
+KE_WF3, KE_WF1, KE_WF2, KE_WF3N, KE_WP, KE_WG = range(6)
 
 
 _D = C.POINTER(C.c_double)
@@ -67,6 +73,13 @@ def lib():
             L.orc_wp.restype = C.c_double
             L.orc_wp.argtypes = [C.c_double]
             L.orc_wf3_split.argtypes = [C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_wf1_split.argtypes = [C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_wf2_split.argtypes = [C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_wg.restype = C.c_double
+            L.orc_wg.argtypes = [C.c_double]
+            L.orc_wg_weights.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_wf3n_weights.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_int32, _D]
+            L.orc_eps_weights.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32, _D]
             L.orc_wp_weights.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_int32, _D]
             L.orc_table_key.restype = C.c_int32
             L.orc_table_key.argtypes = [C.c_int64] * 4
@@ -145,6 +158,40 @@ def wp_weights(d: float, h: float, nr: int, eta_r: int) -> np.ndarray:
 def wf3_split(d: float, nr: int, eta_r: int) -> np.ndarray:
     out = np.zeros(nr)
     lib().orc_wf3_split(d, nr, eta_r, _p(out))
+    return out
+
+
+def wg(x: float) -> float:
+    return float(lib().orc_wg(x))
+
+
+def wg_weights(d: float, h: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_wg_weights(d, h, nr, eta_r, _p(out))
+    return out
+
+
+def wf1_split(d: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_wf1_split(d, nr, eta_r, _p(out))
+    return out
+
+
+def wf2_split(d: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_wf2_split(d, nr, eta_r, _p(out))
+    return out
+
+
+def wf3n_weights(d: float, h: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_wf3n_weights(d, h, nr, eta_r, _p(out))
+    return out
+
+
+def eps_weights(kind: int, d: float, h: float, nr: int, eta_r: int) -> np.ndarray:
+    out = np.zeros(nr)
+    lib().orc_eps_weights(kind, d, h, nr, eta_r, _p(out))
     return out
 
 

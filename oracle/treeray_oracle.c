@@ -50,6 +50,17 @@
  *     s (finest cells) has volume s^3 and mass n_H s^3; the target sphere of
  *     such a cell has r_tp = s/2; a parent sums its eight children, and a
  *     leaf (an AMR cell) is never opened.
+ *  R11 kernel variants (App. A): W_g is normalised over the evaluation points
+ *     like W_p, with the same linear split when no point is inside its
+ *     support.  The two-point flux kernels W_f,1 / W_f,2 / W_f,3 use the
+ *     bracket r_i <= d < r_{i+1}; with d < r_1 everything goes to r_1.
+ *     W_f,2 needs r_{i-1} > 0: at i = 1 its two conditions coincide, and
+ *     there W_f,3 is used.  The generalised W_f,3 spans the points i >= 1
+ *     with |r_i - d| < (sqrt3/2) h; the printed A_2 sums (i - 1)/r_i^2, read
+ *     as (offset from the lowest index)/r_i^2, which is what the two
+ *     conditions give; with N <= 2 points, or when the linear prescription
+ *     makes a weight negative, the two-point W_f,3 is used (emission stays
+ *     non-negative and both conditions still hold).
  */
 #include "treeray_oracle.h"
 
@@ -168,6 +179,12 @@ double orc_wp(double x)
     return 0.0;
 }
 
+double orc_wg(double x)
+{   /* Eq. A1: Gaussian truncated at sqrt3/2 */
+    x = fabs(x);
+    return x < 0.5 * sqrt(3.0) ? exp(-x * x) : 0.0;
+}
+
 /* index i with r_i <= d < r_{i+1}, for r_0 <= d < r_{nr-1} */
 static int32_t bracket(double d, int32_t nr, int32_t eta_r)
 {
@@ -176,15 +193,16 @@ static int32_t bracket(double d, int32_t nr, int32_t eta_r)
     return i;
 }
 
-void orc_wp_weights(double d, double h, int32_t nr, int32_t eta_r, double* w)
-{   /* W_p normalised so that the weights over all evaluation points sum to
-     * one (App. A, kernel tabulation paragraph); reading R5/R6 for the edges */
+static void smooth_weights(int32_t gauss, double d, double h, int32_t nr, int32_t eta_r, double* w)
+{   /* W_p or W_g normalised so that the weights over all evaluation points
+     * sum to one (App. A, kernel tabulation paragraph); readings R5, R6, R11 */
     for (int32_t i = 0; i < nr; ++i) w[i] = 0.0;
     double rlast = orc_radius(nr - 1, eta_r);
     if (d >= rlast) { w[nr - 1] = 1.0; return; }
     double S = 0.0;
     for (int32_t i = 0; i < nr; ++i) {
-        double W = orc_wp((orc_radius(i, eta_r) - d) / h);
+        double x = (orc_radius(i, eta_r) - d) / h;
+        double W = gauss ? orc_wg(x) : orc_wp(x);
         w[i] = W;
         S += W;
     }
@@ -196,6 +214,16 @@ void orc_wp_weights(double d, double h, int32_t nr, int32_t eta_r, double* w)
     double ri = orc_radius(i, eta_r), rj = orc_radius(i + 1, eta_r);
     w[i] = (rj - d) / (rj - ri);
     w[i + 1] = (d - ri) / (rj - ri);
+}
+
+void orc_wp_weights(double d, double h, int32_t nr, int32_t eta_r, double* w)
+{
+    smooth_weights(0, d, h, nr, eta_r, w);
+}
+
+void orc_wg_weights(double d, double h, int32_t nr, int32_t eta_r, double* w)
+{
+    smooth_weights(1, d, h, nr, eta_r, w);
 }
 
 void orc_wf3_split(double d, int32_t nr, int32_t eta_r, double* w)
@@ -211,6 +239,77 @@ void orc_wf3_split(double d, int32_t nr, int32_t eta_r, double* w)
     double wj = (a - t) / (a - b);
     w[i + 1] = wj;
     w[i] = 1.0 - wj;
+}
+
+void orc_wf1_split(double d, int32_t nr, int32_t eta_r, double* w)
+{   /* W_f,1 (App. A.3): w_{i+1} / w_i = (d - r_i) / (r_{i+1} - d) and the
+     * flux at r = 0 exact, w_i / r_i^2 + w_{i+1} / r_{i+1}^2 = 1 / d^2 */
+    for (int32_t i = 0; i < nr; ++i) w[i] = 0.0;
+    double rlast = orc_radius(nr - 1, eta_r);
+    if (d >= rlast) { w[nr - 1] = 1.0; return; }
+    int32_t i = bracket(d, nr, eta_r);
+    if (i == 0) { w[1] = 1.0; return; }
+    double ri = orc_radius(i, eta_r), rj = orc_radius(i + 1, eta_r);
+    double ratio = (d - ri) / (rj - d);
+    double wi = 1.0 / ((d * d) * (1.0 / (ri * ri) + ratio / (rj * rj)));
+    w[i] = wi;
+    w[i + 1] = ratio * wi;
+}
+
+void orc_wf2_split(double d, int32_t nr, int32_t eta_r, double* w)
+{   /* W_f,2 (App. A.3): the flux exact at r = 0 and at r_{i-1}:
+     * w_i / r_i^2 + w_{i+1} / r_{i+1}^2 = 1 / d^2 and
+     * w_i / (r_i - r_{i-1})^2 + w_{i+1} / (r_{i+1} - r_{i-1})^2 = 1 / (d - r_{i-1})^2,
+     * solved by Cramer's rule; reading R11 where it does not apply */
+    double rlast = orc_radius(nr - 1, eta_r);
+    int32_t i = d >= rlast ? nr - 1 : bracket(d, nr, eta_r);
+    if (d >= rlast || i < 2) { orc_wf3_split(d, nr, eta_r, w); return; }
+    for (int32_t k = 0; k < nr; ++k) w[k] = 0.0;
+    double rm = orc_radius(i - 1, eta_r), ri = orc_radius(i, eta_r), rj = orc_radius(i + 1, eta_r);
+    double a11 = 1.0 / (ri * ri), a12 = 1.0 / (rj * rj), b1 = 1.0 / (d * d);
+    double a21 = 1.0 / ((ri - rm) * (ri - rm)), a22 = 1.0 / ((rj - rm) * (rj - rm)), b2 = 1.0 / ((d - rm) * (d - rm));
+    double det = a11 * a22 - a12 * a21;
+    double wi = (b1 * a22 - a12 * b2) / det;
+    double wj = (a11 * b2 - a21 * b1) / det;
+    if (!(wi >= 0.0 && wj >= 0.0)) { orc_wf3_split(d, nr, eta_r, w); return; }
+    w[i] = wi;
+    w[i + 1] = wj;
+}
+
+void orc_wf3n_weights(double d, double h, int32_t nr, int32_t eta_r, double* w)
+{   /* generalised W_f,3 (Eq. A8-A10): the N points in the support carry
+     * eps (a + b k), k = offset from the lowest index, with the sum and the
+     * flux at r = 0 exact; reading R11 for A_2 and the fallback */
+    double rlast = orc_radius(nr - 1, eta_r);
+    if (d >= rlast) { orc_wf3_split(d, nr, eta_r, w); return; }
+    int32_t lo = -1, n = 0;
+    for (int32_t i = 1; i < nr; ++i)
+        if (fabs(orc_radius(i, eta_r) - d) < 0.5 * sqrt(3.0) * h) { if (lo < 0) lo = i; n++; }
+    if (n <= 2) { orc_wf3_split(d, nr, eta_r, w); return; }
+    double A1 = 0.0, A2 = 0.0;
+    for (int32_t k = 0; k < n; ++k) {
+        double r = orc_radius(lo + k, eta_r);
+        A1 += 1.0 / (r * r);
+        A2 += (double)k / (r * r);
+    }
+    double b = (1.0 / (d * d) - A1 / (double)n) / (A2 - (double)(n - 1) * A1 / 2.0);
+    double a = 1.0 / (double)n - b * (double)(n - 1) / 2.0;
+    for (int32_t k = 0; k < n; ++k)
+        if (a + b * (double)k < 0.0) { orc_wf3_split(d, nr, eta_r, w); return; }
+    for (int32_t i = 0; i < nr; ++i) w[i] = 0.0;
+    for (int32_t k = 0; k < n; ++k) w[lo + k] = a + b * (double)k;
+}
+
+void orc_eps_weights(int32_t kind, double d, double h, int32_t nr, int32_t eta_r, double* w)
+{
+    switch (kind) {
+    case ORC_KE_WF1: orc_wf1_split(d, nr, eta_r, w); break;
+    case ORC_KE_WF2: orc_wf2_split(d, nr, eta_r, w); break;
+    case ORC_KE_WF3N: orc_wf3n_weights(d, h, nr, eta_r, w); break;
+    case ORC_KE_WP: orc_wp_weights(d, h, nr, eta_r, w); break;
+    case ORC_KE_WG: orc_wg_weights(d, h, nr, eta_r, w); break;
+    default: orc_wf3_split(d, nr, eta_r, w); break;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -674,9 +773,9 @@ static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t
     const orc_entry* ent = table_entry(p->nside, orc_table_key(ox, oy, oz, s));
     int32_t nr = w->nr;
     double h = (double)s;
-    if (nd->alpha != 0.0) orc_wp_weights(d, h, nr, p->eta_r, w->wa);
-    if (nd->eps != 0.0) orc_wf3_split(d, nr, p->eta_r, w->we);
-    if (use_e && nd->e != 0.0) orc_wp_weights(d, h, nr, p->eta_r, w->wee);
+    if (nd->alpha != 0.0) smooth_weights(p->kernel_alpha == ORC_K_WG, d, h, nr, p->eta_r, w->wa);
+    if (nd->eps != 0.0) orc_eps_weights(p->kernel_eps, d, h, nr, p->eta_r, w->we);
+    if (use_e && nd->e != 0.0) smooth_weights(p->kernel_alpha == ORC_K_WG, d, h, nr, p->eta_r, w->wee);
     const double inv_m3 = 1.0 / (double)(ORC_TM * ORC_TM * ORC_TM);
     for (int32_t j = 0; j < ent->n; ++j) {
         double wk = (double)ent->cnt[j] * inv_m3;     /* volume fraction in ray k */

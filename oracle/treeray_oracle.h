@@ -35,7 +35,13 @@ typedef struct {
     double alpha_B;       /* case-B recombination coefficient, cm^3 s^-1 */
     double hnu;           /* mean EUV photon energy, erg */
     int32_t zeta_g;       /* 1: apply the geometric correction (Eq. 16) */
+    int32_t kernel_alpha; /* radial kernel for alpha and e: ORC_K_WP or ORC_K_WG */
+    int32_t kernel_eps;   /* radial kernel for eps: ORC_KE_* */
 } orc_params;
+
+/* kernel choices (App. A) */
+enum { ORC_K_WP = 0, ORC_K_WG = 1 };
+enum { ORC_KE_WF3 = 0, ORC_KE_WF1 = 1, ORC_KE_WF2 = 2, ORC_KE_WF3N = 3, ORC_KE_WP = 4, ORC_KE_WG = 5 };
 
 typedef struct orc_tree orc_tree;
 
@@ -51,6 +57,13 @@ double orc_radius(int32_t i, int32_t eta_r);
 double orc_wp(double x);
 void orc_wf3_split(double d, int32_t nr, int32_t eta_r, double* w_out);
 void orc_wp_weights(double d, double h, int32_t nr, int32_t eta_r, double* w_out);
+double orc_wg(double x);
+void orc_wg_weights(double d, double h, int32_t nr, int32_t eta_r, double* w_out);
+void orc_wf1_split(double d, int32_t nr, int32_t eta_r, double* w_out);
+void orc_wf2_split(double d, int32_t nr, int32_t eta_r, double* w_out);
+void orc_wf3n_weights(double d, double h, int32_t nr, int32_t eta_r, double* w_out);
+/* weights of eps for a kernel choice ORC_KE_* */
+void orc_eps_weights(int32_t kind, double d, double h, int32_t nr, int32_t eta_r, double* w_out);
 
 /* node->ray table */
 int32_t orc_table_key(int64_t ox, int64_t oy, int64_t oz, int64_t s);

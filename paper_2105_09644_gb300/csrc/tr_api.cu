@@ -54,6 +54,10 @@ tr_status check_params(const tr_params* p) {
         return set_error(TR_EINVAL, "precision must be TR_FP64 or TR_FP32_SWEEP64");
     if (p->max_iter < 1) return set_error(TR_EINVAL, "max_iter must be >= 1");
     if (p->delta_mode != 0 && p->delta_mode != 1) return set_error(TR_EINVAL, "delta_mode must be 0 or 1");
+    if (p->kernel_alpha != TR_KERNEL_WP && p->kernel_alpha != TR_KERNEL_WG)
+        return set_error(TR_EINVAL, "kernel_alpha must be TR_KERNEL_WP or TR_KERNEL_WG (got %d)", p->kernel_alpha);
+    if (p->kernel_eps < TR_EPS_WF3 || p->kernel_eps > TR_EPS_WG)
+        return set_error(TR_EINVAL, "kernel_eps must be one of tr_eps_kernel (got %d)", p->kernel_eps);
     return TR_OK;
 }
 
@@ -351,6 +355,8 @@ void tr_params_default(tr_params* p) {
     p->max_iter = 1;
     p->precision = TR_FP64;
     p->zeta_g = 1;
+    p->kernel_alpha = TR_KERNEL_WP;
+    p->kernel_eps = TR_EPS_WF3;
 }
 
 const char* tr_last_error(void) { return g_err; }

@@ -88,6 +88,10 @@ extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, con
         return set_error(TR_EINVAL, "eta_r must be 1, 2, 4 or 8 (got %d)", p->eta_r);
     if (p->precision != TR_FP64 && p->precision != TR_FP32_SWEEP64)
         return set_error(TR_EINVAL, "precision must be TR_FP64 or TR_FP32_SWEEP64");
+    if (p->kernel_alpha != TR_KERNEL_WP && p->kernel_alpha != TR_KERNEL_WG)
+        return set_error(TR_EINVAL, "kernel_alpha must be TR_KERNEL_WP or TR_KERNEL_WG");
+    if (p->kernel_eps < TR_EPS_WF3 || p->kernel_eps > TR_EPS_WG)
+        return set_error(TR_EINVAL, "kernel_eps must be one of tr_eps_kernel");
     if (!(p->alpha_B > 0.0) || !(p->hnu > 0.0) || !(g->dx > 0.0) || !std::isfinite(g->dx))
         return set_error(TR_EINVAL, "alpha_B, hnu and dx must be > 0");
     if (s && s->n < 0) return set_error(TR_EINVAL, "negative source count");

@@ -56,6 +56,7 @@ struct WalkArgs {
     const int4* blk;                        // AMR tree: per block {cell level, x, y, z}
     const uint32_t* blk_order;              // AMR tree: blocks in walk order
     int64_t n_cells;                        // valid target indices are [0, n_cells)
+    int kern_a, kern_e;                     // tr_kernel (alpha, e) and tr_eps_kernel (eps)
     int64_t n_targets;
     double Fconv, Econv;                    // scaled flux -> CGS flux / energy density
     double* F;
@@ -87,6 +88,23 @@ __device__ __forceinline__ T wp_kernel(T x) {
     if (x < T(0.5)) return M + x * x * (a1 * x - (T(0.5) * a1 + T(4.0) * (M - A)));
     if (x < s3h) { T t = x - s3h; return t * t * (a2 * x + c2); }
     return T(0);
+}
+
+// W_g of App. A (Eq. A1): exp(-x^2), truncated at sqrt3/2.
+constexpr double S3H_D = 0.86602540378443864676;
+
+template <typename T>
+__device__ __forceinline__ T wg_kernel(T x) {
+    return x < T(S3H_D) ? exp(-x * x) : T(0);
+}
+
+// The smoothing kernel of alpha and e at distance `dist` from the node:
+// W_p(dist / h) with hpar = 1/h, or W_g(dist / h) with hpar = h (a true
+// division, since W_g jumps at its truncation and the argument must round
+// as the definition's quotient does).
+template <typename T>
+__device__ __forceinline__ T radial_w(T dist, T hpar, int gauss) {
+    return gauss ? wg_kernel<T>(dist / hpar) : wp_kernel<T>(dist * hpar);
 }
 
 __device__ __forceinline__ int face_bin(int x, int A) {
@@ -232,10 +250,10 @@ constexpr int MAXW = 12;                    // W_p values kept per node (longer 
 template <int MODE>
 __device__ __forceinline__ typename Prec<MODE>::real spread_weight(const RadialSpread<MODE>& n, int j,
                                                                  const typename Prec<MODE>::real* r,
-                                                                 const typename Prec<MODE>::real* wts) {
+                                                                 const typename Prec<MODE>::real* wts, int gauss) {
     using real = typename Prec<MODE>::real;
     if (n.kind == 3) return wts[n.src * MAXW + n.woff + j] * n.b;
-    if (n.kind == 0) return wp_kernel<real>(fabs(r[n.lo + j] - n.d) * n.a) * n.b;
+    if (n.kind == 0) return radial_w<real>(fabs(r[n.lo + j] - n.d), n.a, gauss) * n.b;
     if (n.kind == 1) return real(1);
     return j == 0 ? n.a : n.b;
 }
@@ -243,8 +261,8 @@ __device__ __forceinline__ typename Prec<MODE>::real spread_weight(const RadialS
 // W_p normalisation of an accepted node: the support of the kernel on the
 // evaluation points and 1/S.
 template <int MODE>
-__device__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename Prec<MODE>::real d, int s,
-                             typename Prec<MODE>::real* wrow) {
+__device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename Prec<MODE>::real d,
+                                             int s, typename Prec<MODE>::real* wrow, int gauss) {
     using real = typename Prec<MODE>::real;
     const int nr = a.nr;
     const real* r = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
@@ -254,6 +272,7 @@ __device__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename 
         return;
     }
     const real h = (real)s, inv_h = real(1) / h;
+    const real hpar = gauss ? h : inv_h;
     const real reach = real(0.8661) * h;
     const real dlo = d > reach ? d - reach : real(0);
     const int lo = max((int)floor((real)a.eta * sqrt(real(2) * dlo)) - 1, 0);
@@ -262,13 +281,13 @@ __device__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename 
     int first = hi + 1, last = lo - 1;
     const bool keep = MODE == 0 && hi - lo + 1 <= MAXW;
     for (int i = lo; i <= hi; ++i) {
-        const real w = wp_kernel<real>(fabs(r[i] - d) * inv_h);
+        const real w = radial_w<real>(fabs(r[i] - d), hpar, gauss);
         if (keep) wrow[i - lo] = w;
         if (w > real(0)) { S += w; first = min(first, i); last = i; }
     }
     if (S > real(0)) {
         n.kind = keep ? 3 : 0; n.woff = (uint8_t)(first - lo);
-        n.lo = (int16_t)first; n.npts = (int16_t)(last - first + 1); n.a = inv_h; n.b = real(1) / S;
+        n.lo = (int16_t)first; n.npts = (int16_t)(last - first + 1); n.a = hpar; n.b = real(1) / S;
         return;
     }
     int i = min(max((int)floor((real)a.eta * sqrt(real(2) * d)), 0), nr - 2);
@@ -280,14 +299,138 @@ __device__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename 
     n.b = (d - ra) / (rb - ra);
 }
 
-// W_f,3 (App. A.3) deposit of an emitting node: two points r_i <= d < r_{i+1}
-// keeping the sum and the flux at the target exact.  Emitting nodes are few
-// (they contain a source), so the accepting thread does it alone.
+// The other eps kernels (App. A.3), in FP64 whatever the form: emitting
+// nodes are few.  The weights of points lo .. lo+n-1 are p0, p1 (two
+// points), a + b k (generalised W_f,3, p0 = a, p1 = b) or a smoothing
+// kernel over 1/S (p0).
+struct EpsSpread {
+    int lo, n, kind;                        // kind 0 two points, 1 linear, 2 W_p, 3 W_g
+    double p0, p1, d, h;
+};
+
+__device__ __forceinline__ int bracket_d(const double* r, int nr, int eta, double d) {
+    int i = min(max((int)floor((double)eta * sqrt(2.0 * d)), 0), nr - 2);
+    while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
+    while (i > 0 && r[i] > d) --i;
+    return i;
+}
+
+// two-point W_f,3: the sum and the flux at r = 0 exact
+__device__ void eps_wf3(const double* r, int nr, int eta, double d, EpsSpread& s) {
+    s.kind = 0;
+    if (d >= r[nr - 1]) { s.lo = nr - 1; s.n = 1; s.p0 = 1.0; return; }
+    const int i = bracket_d(r, nr, eta, d);
+    if (i == 0) { s.lo = 1; s.n = 1; s.p0 = 1.0; return; }
+    const double ri = r[i], rj = r[i + 1];
+    const double ia = 1.0 / (ri * ri), ib = 1.0 / (rj * rj), it = 1.0 / (d * d);
+    const double w1 = (ia - it) / (ia - ib);
+    s.lo = i; s.n = 2; s.p0 = 1.0 - w1; s.p1 = w1;
+}
+
+__device__ void eps_setup(const WalkArgs& a, double d, double h, EpsSpread& s) {
+    const double* r = a.r;
+    const int nr = a.nr, eta = a.eta;
+    s.d = d; s.h = h;
+    if (a.kern_e == TR_EPS_WF1 || a.kern_e == TR_EPS_WF2) {
+        // W_f,1: w_{i+1} / w_i = (d - r_i) / (r_{i+1} - d); W_f,2: the flux also
+        // exact at r_{i-1}; both with the flux at r = 0 exact
+        const int i = d >= r[nr - 1] ? nr - 1 : bracket_d(r, nr, eta, d);
+        if (d >= r[nr - 1] || i == 0 || (a.kern_e == TR_EPS_WF2 && i < 2)) { eps_wf3(r, nr, eta, d, s); return; }
+        const double ri = r[i], rj = r[i + 1];
+        double w0, w1;
+        if (a.kern_e == TR_EPS_WF1) {
+            const double ratio = (d - ri) / (rj - d);
+            w0 = 1.0 / ((d * d) * (1.0 / (ri * ri) + ratio / (rj * rj)));
+            w1 = ratio * w0;
+        } else {
+            const double rm = r[i - 1];
+            const double a11 = 1.0 / (ri * ri), a12 = 1.0 / (rj * rj), b1 = 1.0 / (d * d);
+            const double a21 = 1.0 / ((ri - rm) * (ri - rm)), a22 = 1.0 / ((rj - rm) * (rj - rm));
+            const double b2 = 1.0 / ((d - rm) * (d - rm));
+            const double det = a11 * a22 - a12 * a21;
+            w0 = (b1 * a22 - a12 * b2) / det;
+            w1 = (a11 * b2 - a21 * b1) / det;
+            if (!(w0 >= 0.0 && w1 >= 0.0)) { eps_wf3(r, nr, eta, d, s); return; }
+        }
+        s.kind = 0; s.lo = i; s.n = 2; s.p0 = w0; s.p1 = w1;
+        return;
+    }
+    if (a.kern_e == TR_EPS_WF3N) {
+        // Eq. A8-A10 over the points i >= 1 inside the support
+        if (d >= r[nr - 1]) { eps_wf3(r, nr, eta, d, s); return; }
+        int lo = -1, n = 0;
+        for (int i = 1; i < nr; ++i)
+            if (fabs(r[i] - d) < S3H_D * h) { if (lo < 0) lo = i; ++n; }
+        if (n <= 2) { eps_wf3(r, nr, eta, d, s); return; }
+        double A1 = 0.0, A2 = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double rk = r[lo + k];
+            A1 += 1.0 / (rk * rk);
+            A2 += (double)k / (rk * rk);
+        }
+        const double b = (1.0 / (d * d) - A1 / (double)n) / (A2 - (double)(n - 1) * A1 / 2.0);
+        const double c = 1.0 / (double)n - b * (double)(n - 1) / 2.0;
+        if (c < 0.0 || c + b * (double)(n - 1) < 0.0) { eps_wf3(r, nr, eta, d, s); return; }   // linear: ends suffice
+        s.kind = 1; s.lo = lo; s.n = n; s.p0 = c; s.p1 = b;
+        return;
+    }
+    // W_p or W_g normalised over the points, as for alpha
+    const int gauss = a.kern_e == TR_EPS_WG;
+    if (d >= r[nr - 1]) { s.kind = 0; s.lo = nr - 1; s.n = 1; s.p0 = 1.0; return; }
+    double S = 0.0;
+    int first = nr, last = -1;
+    for (int i = 0; i < nr; ++i) {
+        const double x = fabs(r[i] - d) / h;
+        const double w = gauss ? wg_kernel<double>(x) : wp_kernel<double>(x);
+        if (w > 0.0) { S += w; first = min(first, i); last = i; }
+    }
+    if (S > 0.0) { s.kind = gauss ? 3 : 2; s.lo = first; s.n = last - first + 1; s.p0 = 1.0 / S; return; }
+    const int i = bracket_d(r, nr, eta, d);
+    s.kind = 0; s.lo = i; s.n = 2;
+    s.p0 = (r[i + 1] - d) / (r[i + 1] - r[i]);
+    s.p1 = (d - r[i]) / (r[i + 1] - r[i]);
+}
+
+__device__ __forceinline__ double eps_weight(const EpsSpread& s, const double* r, int j) {
+    if (s.kind == 0) return j == 0 ? s.p0 : s.p1;
+    if (s.kind == 1) return s.p0 + s.p1 * (double)j;
+    const double x = fabs(r[s.lo + j] - s.d) / s.h;
+    return (s.kind == 3 ? wg_kernel<double>(x) : wp_kernel<double>(x)) * s.p0;
+}
+
+// eps deposit with a kernel other than the default.
 template <int MODE>
-__device__ void deposit_eps(const WalkArgs& a, double* bins_eps, uint32_t off, int ne,
-                            typename Prec<MODE>::real d, typename Prec<MODE>::real eps, float scale) {
+__device__ __forceinline__ void deposit_eps_variant(const WalkArgs& a, double* bins_eps, uint32_t off, int ne, double d,
+                                                 typename Prec<MODE>::real eps, float scale, int s_edge) {
     using real = typename Prec<MODE>::real;
     const int nr = a.nr;
+    EpsSpread sp;
+    eps_setup(a, d, (double)s_edge, sp);
+    const real inv_m3v = real(1.0) / real(TM * TM * TM);
+    for (int k = 0; k < ne; ++k) {
+        const uint32_t en = __ldg(a.tent + off + k);
+        const int b = (int)(en >> 16) * nr + sp.lo;
+        const real wk = (real)(en & 0xffffu) * inv_m3v;
+        for (int j = 0; j < sp.n; ++j) {
+            const real w = (real)eps_weight(sp, a.r, j);
+            if (w != real(0)) bin_atomic_add<MODE>(bins_eps + b + j, wk * w * eps, scale);
+        }
+    }
+}
+
+// Deposit of an emitting node's eps (App. A.3).  Default W_f,3: two points
+// r_i <= d < r_{i+1} keeping the sum and the flux at the target exact.
+// Emitting nodes are few (they contain a source), so the accepting thread
+// does it alone.
+template <int MODE, bool VAR>
+__device__ void deposit_eps(const WalkArgs& a, double* bins_eps, uint32_t off, int ne,
+                            typename Prec<MODE>::real d, typename Prec<MODE>::real eps, float scale, int s_edge) {
+    using real = typename Prec<MODE>::real;
+    const int nr = a.nr;
+    if (VAR && a.kern_e != TR_EPS_WF3) {
+        deposit_eps_variant<MODE>(a, bins_eps, off, ne, (double)d, eps, scale, s_edge);
+        return;
+    }
     const real* r = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
     int i;
     real w0, w1;
@@ -592,7 +735,9 @@ __device__ __forceinline__ void flush_counters(const WalkArgs& a, unsigned long 
 // jobs (a job = one tree and a range or list of its cells).  Several trees in
 // one launch is how independent requests are batched together.  Each step
 // pops NT/8 opened nodes and evaluates their NT children, one per thread.
-template <int MODE, bool DUMP, int NT>
+// VAR: the kernel choices other than W_p / W_f,3 are compiled in (a
+// separate instantiation, so that the default walk keeps its registers).
+template <int MODE, bool DUMP, int NT, bool VAR>
 __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
                                             int n_jobs, unsigned int* counter) {
     using real = typename Prec<MODE>::real;
@@ -744,9 +889,9 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                             const uint2 hd = __ldg(a.hdr + key);
                             ne = (int)hd.y;
                             n_ent += ne;
-                            if (qv[1] != real(0)) deposit_eps<MODE>(a, bins_eps, hd.x, ne, d, qv[1], sc.eps);
+                            if (qv[1] != real(0)) deposit_eps<MODE, VAR>(a, bins_eps, hd.x, ne, d, qv[1], sc.eps, s);
                             if (has_ae && ne > 0) {
-                                radial_setup<MODE>(a, node, d, s, s_w + tid * MAXW);
+                                radial_setup<MODE>(a, node, d, s, s_w + tid * MAXW, VAR ? a.kern_a : 0);
                                 node.src = (uint16_t)tid;
                                 node.alpha = qv[0];
                                 node.e = a.use_e ? qv[2] : real(0);
@@ -813,7 +958,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                         const int b0 = (int)(en >> 16) * nr + n.lo;
                         const real wk = (real)(en & 0xffffu) * inv_m3;
                         for (int j = 0; j < n.npts; ++j) {
-                            const real w = spread_weight<MODE>(n, j, rr, s_w) * wk;
+                            const real w = spread_weight<MODE>(n, j, rr, s_w, VAR ? a.kern_a : 0) * wk;
                             if (w == real(0)) continue;
                             if (n.alpha != real(0)) bin_atomic_add<MODE>(bins_a + b0 + j, w * n.alpha, sc.a);
                             if (a.use_e && n.e != real(0)) bin_atomic_add<MODE>(bins_e + b0 + j, w * n.e, sc.e);
@@ -933,6 +1078,8 @@ WalkArgs make_args(const tr_tree* t) {
     a.status = t->status;
     a.stats = t->stats;
     a.n_cells = t->n_cells;
+    a.kern_a = t->p.kernel_alpha;
+    a.kern_e = t->p.kernel_eps;
     a.flags = t->flags;
     a.blk = t->blk;
     a.blk_order = t->blk_order;
@@ -974,7 +1121,7 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const i
 
 bool wide_ctas(int mode, size_t smem) {
     int per_sm = 0;
-    const void* k = mode == 0 ? (const void*)k_walk<0, false, WALK_NT> : (const void*)k_walk<1, false, WALK_NT>;
+    const void* k = mode == 0 ? (const void*)k_walk<0, false, WALK_NT, false> : (const void*)k_walk<1, false, WALK_NT, false>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WALK_NT, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -983,23 +1130,33 @@ bool wide_ctas(int mode, size_t smem) {
     return per_sm < 3;
 }
 
-tr_status launch_jobs(int mode, bool dump, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
-                      int64_t total, unsigned int* counter, cudaStream_t st) {
-    constexpr int W0 = WALK_NT_WIDE_F64, W1 = WALK_NT_WIDE_F32;
-    if (wide_ctas(mode, smem)) {
+template <bool VAR>
+tr_status launch_jobs_v(int mode, bool dump, bool wide, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
+                        int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
+    constexpr int W0 = WALK_NT_WIDE_F64, W1 = WALK_NT_WIDE_F32, T = WALK_NT;
+    if (wide) {
         if (mode == 0)
-            return dump ? launch_persistent<W0>(k_walk<0, true, W0>, smem, jobs, job_end, n_jobs, total, counter, st)
-                        : launch_persistent<W0>(k_walk<0, false, W0>, smem, jobs, job_end, n_jobs, total, counter, st);
-        return dump ? launch_persistent<W1>(k_walk<1, true, W1>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent<W1>(k_walk<1, false, W1>, smem, jobs, job_end, n_jobs, total, counter, st);
+            return dump ? launch_persistent<W0>(k_walk<0, true, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                        : launch_persistent<W0>(k_walk<0, false, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+        return dump ? launch_persistent<W1>(k_walk<1, true, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent<W1>(k_walk<1, false, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
     }
-    constexpr int T = WALK_NT;
     if (mode == 0)
-        return dump ? launch_persistent<T>(k_walk<0, true, T>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent<T>(k_walk<0, false, T>, smem, jobs, job_end, n_jobs, total, counter, st);
-    return dump ? launch_persistent<T>(k_walk<1, true, T>, smem, jobs, job_end, n_jobs, total, counter, st)
-                : launch_persistent<T>(k_walk<1, false, T>, smem, jobs, job_end, n_jobs, total, counter, st);
+        return dump ? launch_persistent<T>(k_walk<0, true, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent<T>(k_walk<0, false, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    return dump ? launch_persistent<T>(k_walk<1, true, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                : launch_persistent<T>(k_walk<1, false, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
 }
+
+// var: some job uses a kernel choice other than W_p / W_f,3
+tr_status launch_jobs(int mode, bool dump, bool var, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
+                      int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
+    const bool wide = wide_ctas(mode, smem);
+    return var ? launch_jobs_v<true>(mode, dump, wide, smem, jobs, job_end, n_jobs, total, counter, st)
+               : launch_jobs_v<false>(mode, dump, wide, smem, jobs, job_end, n_jobs, total, counter, st);
+}
+
+bool uses_variants(const tr_tree* t) { return t->p.kernel_alpha != TR_KERNEL_WP || t->p.kernel_eps != TR_EPS_WF3; }
 
 }  // namespace
 
@@ -1027,7 +1184,7 @@ tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, 
     if (s != TR_OK || n_targets <= 0) return s;
     const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(t->jobbuf);
     const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<const unsigned char*>(t->jobbuf) + sizeof(WalkArgs));
-    return launch_jobs(t->mode, dump, walk_smem(t), jobs, job_end, 1, n_targets, t->counter, st);
+    return launch_jobs(t->mode, dump, uses_variants(t), walk_smem(t), jobs, job_end, 1, n_targets, t->counter, st);
 }
 
 tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, const int64_t* count, int n,
@@ -1038,8 +1195,10 @@ tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, cons
     int64_t* he = reinterpret_cast<int64_t*>(host.data() + (size_t)n * sizeof(WalkArgs));
     size_t smem = 0;
     int64_t total = 0;
+    bool var = false;
     tr_status s = TR_OK;
     for (int i = 0; i < n; ++i) {
+        var = var || uses_variants(trees[i]);
         WalkArgs a = make_args(trees[i]);
         a.targets = nullptr;
         a.first = first[i];
@@ -1057,7 +1216,7 @@ tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, cons
     if (s != TR_OK || total == 0) return s;
     const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(jobbuf);
     const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<unsigned char*>(jobbuf) + (size_t)n * sizeof(WalkArgs));
-    return launch_jobs(trees[0]->mode, false, smem, jobs, job_end, n, total, counter, st);
+    return launch_jobs(trees[0]->mode, false, var, smem, jobs, job_end, n, total, counter, st);
 }
 
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st) {

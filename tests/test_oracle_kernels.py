@@ -116,3 +116,116 @@ def test_wf3_error_histogram_shape(orc):
             errs.append(abs(approx - 1.0 / (d - r[j]) ** 2) * (d - r[j]) ** 2)
     errs = np.array(errs)
     assert np.median(errs) < 0.1
+
+
+def _radii(orc, nr, eta=2):
+    return np.array([orc.radius(i, eta) for i in range(nr)])
+
+
+def test_wg_is_a_normal_density(orc):
+    """W_g (Eq. A1) normalised over the points inside its support is the
+    normal density with variance 1/2 (scipy), renormalised there."""
+    from scipy.stats import norm
+    nr = 43
+    r = _radii(orc, nr)
+    rng = np.random.default_rng(7)
+    assert orc.wg(0.0) == 1.0 and orc.wg(S3H) == 0.0 and orc.wg(-0.3) == orc.wg(0.3)
+    for _ in range(200):
+        d = rng.uniform(0.5, r[-1] * 0.999)
+        h = 2.0 ** rng.integers(0, 6)
+        w = orc.wg_weights(d, h, nr, 2)
+        assert w.sum() == pytest.approx(1.0, abs=1e-13)
+        x = (r - d) / h
+        inside = np.abs(x) < S3H
+        if not inside.any():
+            continue
+        want = norm.pdf(x[inside], scale=1 / math.sqrt(2.0))
+        np.testing.assert_allclose(w[inside], want / want.sum(), rtol=1e-12)
+        assert np.all(w[~inside] == 0.0)
+
+
+def test_wf1_conditions(orc):
+    """W_f,1 (App. A.3): flux at r = 0 exact, eps_{i+1}/eps_i = (d - r_i)/(r_{i+1} - d)."""
+    nr = 43
+    r = _radii(orc, nr)
+    for d in np.random.default_rng(8).uniform(r[1], r[-1] * 0.999, 400):
+        w = orc.wf1_split(d, nr, 2)
+        i = np.searchsorted(r, d, side="right") - 1
+        assert np.all(np.delete(w, [i, i + 1]) == 0.0) and np.all(w >= 0)
+        assert np.sum(w[1:] / r[1:] ** 2) == pytest.approx(1.0 / d ** 2, rel=1e-12)
+        assert w[i + 1] * (r[i + 1] - d) == pytest.approx(w[i] * (d - r[i]), rel=1e-12, abs=1e-15)
+
+
+def test_wf2_flux_exact_at_target_and_previous_point(orc):
+    """W_f,2 (App. A.3): the flux of the two mapped points equals that of
+    the true source at r = 0 and at r_{i-1}; next to the target (i < 2)
+    the two conditions coincide and W_f,3 is used."""
+    nr = 43
+    r = _radii(orc, nr)
+    for d in np.random.default_rng(9).uniform(r[1], r[-1] * 0.999, 400):
+        w = orc.wf2_split(d, nr, 2)
+        i = np.searchsorted(r, d, side="right") - 1
+        if i < 2:
+            np.testing.assert_array_equal(w, orc.wf3_split(d, nr, 2))
+            continue
+        nz = np.nonzero(w)[0]
+        assert set(nz) <= {i, i + 1} and np.all(w >= 0)
+        assert np.sum(w[nz] / r[nz] ** 2) == pytest.approx(1.0 / d ** 2, rel=1e-11)
+        rm = r[i - 1]
+        assert np.sum(w[nz] / (r[nz] - rm) ** 2) == pytest.approx(1.0 / (d - rm) ** 2, rel=1e-11)
+
+
+def test_wf3_general_linear_and_conserving(orc):
+    """Generalised W_f,3 (Eq. A8-A10): the points in the node's support
+    carry weights linear in their index, summing to one, with the flux at
+    r = 0 exact; otherwise (too few points, a negative weight) the two-point
+    W_f,3."""
+    nr = 59
+    r = _radii(orc, nr)
+    rng = np.random.default_rng(10)
+    n_general = 0
+    for _ in range(600):
+        d = rng.uniform(1.0, r[-1] * 0.999)
+        h = 2.0 ** rng.integers(0, 7)
+        w = orc.wf3n_weights(d, h, nr, 2)
+        nz = np.nonzero(w)[0]
+        assert np.all(w >= 0)
+        assert w.sum() == pytest.approx(1.0, abs=1e-12)
+        assert np.sum(w[1:] / r[1:] ** 2) == pytest.approx(1.0 / d ** 2, rel=1e-10)
+        support = [i for i in range(1, nr) if abs(r[i] - d) < S3H * h]
+        if len(nz) > 2:
+            n_general += 1
+            assert list(nz) == support
+            np.testing.assert_allclose(np.diff(w[nz], 2), 0.0, atol=1e-13)
+        else:
+            np.testing.assert_array_equal(w, orc.wf3_split(d, nr, 2))
+    assert n_general > 100
+
+
+def test_flux_kernels_error_ranking(orc):
+    """App. A, Fig. A3 set-up (sources on a ray with 10 points): W_f,2 gives
+    the smallest flux errors at the other points, W_f,3 stays acceptable,
+    and the smoothing kernel W_p (here h = d/2) is far worse than all the
+    flux kernels."""
+    nr = 10
+    r = _radii(orc, nr)
+    rng = np.random.default_rng(5)
+    ds = rng.uniform(r[2], r[-1] * 0.999, 3000)
+    med = {}
+    for name, f in [("wf1", lambda d: orc.wf1_split(d, nr, 2)), ("wf2", lambda d: orc.wf2_split(d, nr, 2)),
+                    ("wf3", lambda d: orc.wf3_split(d, nr, 2)), ("wp", lambda d: orc.wp_weights(d, 0.5 * d, nr, 2))]:
+        errs = []
+        for d in ds:
+            w = f(d)
+            nz = np.nonzero(w)[0]
+            for j in range(1, nr):
+                if r[j] >= d:
+                    break
+                if r[nz.min()] <= r[j]:
+                    continue
+                approx = np.sum(w[nz] / (r[nz] - r[j]) ** 2)
+                errs.append(abs(approx - 1.0 / (d - r[j]) ** 2) * (d - r[j]) ** 2)
+        med[name] = float(np.median(errs))
+    assert med["wf2"] < min(med["wf1"], med["wf3"])
+    assert med["wf3"] < 0.1
+    assert med["wp"] > 5 * max(med["wf1"], med["wf2"], med["wf3"])
