@@ -28,7 +28,8 @@ def main(argv=None):
     B.load()
     if a.workload.startswith("amr"):
         from workloads.amr import amr_cluster
-        w = amr_cluster()
+        # amr_cluster: base 64^3 refined twice (5.9 M cells); amr_mid: base 16^3 (161,792 cells)
+        w = amr_cluster(N_base=16) if a.workload == "amr_mid" else amr_cluster()
         n = torch.from_numpy(w.n_H.ravel()).cuda()
         grid = B.make_amr_grid(w.N_base, w.max_level, w.blk_level, w.blk_pos, n, w.dx_fine)
         build = B.tr_build_tree_amr
