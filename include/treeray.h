@@ -63,11 +63,20 @@ typedef enum {
     TR_EPS_WF3 = 0, TR_EPS_WF1 = 1, TR_EPS_WF2 = 2, TR_EPS_WF3N = 3, TR_EPS_WP = 4, TR_EPS_WG = 5
 } tr_eps_kernel;
 
+/* Boundary conditions of the walk (Sec. 2.8).  Isolated: nothing outside
+ * the box.  Periodic: every node that does not contain the target is taken
+ * at its copy nearest to the target (geometric centres, per axis).  Corner
+ * of symmetry: the grid is one octant of a problem symmetric about its low
+ * corner; the walk maps the grid and its 7 mirror images through that
+ * corner onto the rays, and L_ray defaults to the diagonal of the mirrored
+ * domain (2 N sqrt3 cells). */
+typedef enum { TR_BC_ISOLATED = 0, TR_BC_PERIODIC = 1, TR_BC_CORNER = 2 } tr_bc;
+
 /* Solver parameters (Sec. 2.2-2.6).  tr_params_default() fills the paper's
  * defaults: theta_lim 0.5, theta_if = theta_src = INFINITY, N_side 2,
  * eta_R 2, L_ray = domain diagonal, alpha_B 2.7e-13, h nu = 13.6 eV,
  * eps_lim 1e-2, delta per cell, one pass, FP64, zeta_g on, W_p for alpha
- * and e, W_f,3 for eps. */
+ * and e, W_f,3 for eps, isolated boundaries. */
 typedef struct {
     double theta_lim;       /* BH opening angle: accept when h/d < theta_lim (Sec. 2.4) */
     double theta_if;        /* IF MAC angle, INFINITY disables (Sec. 2.4) */
@@ -84,6 +93,7 @@ typedef struct {
     int32_t zeta_g;         /* 1: apply the geometric factor zeta_g (Eq. 16) */
     int32_t kernel_alpha;   /* tr_kernel for alpha and e */
     int32_t kernel_eps;     /* tr_eps_kernel for eps */
+    int32_t bc;             /* tr_bc: boundary condition of the walk */
 } tr_params;
 
 /* Uniform cubic grid.  N is a power of two with 8 <= N <= 512.

@@ -44,12 +44,14 @@ class Params(C.Structure):
                 ("eta_r", C.c_int32), ("theta_lim", C.c_double), ("theta_if", C.c_double),
                 ("theta_src", C.c_double), ("lray_cells", C.c_double),
                 ("alpha_B", C.c_double), ("hnu", C.c_double), ("zeta_g", C.c_int32),
-                ("kernel_alpha", C.c_int32), ("kernel_eps", C.c_int32)]
+                ("kernel_alpha", C.c_int32), ("kernel_eps", C.c_int32), ("bc", C.c_int32)]
 
 
 # kernel choices (App. A): kernel_alpha for alpha and e, kernel_eps for eps
 K_WP, K_WG = 0, 1
 KE_WF3, KE_WF1, KE_WF2, KE_WF3N, KE_WP, KE_WG = range(6)
+# boundary conditions of the walk (Sec. 2.8)
+BC_ISOLATED, BC_PERIODIC, BC_CORNER = 0, 1, 2
 
 
 _D = C.POINTER(C.c_double)
@@ -268,7 +270,8 @@ class Tree:
         return nd, a, e
 
     def walk(self, p: Params, target: int, cap: int = 1 << 16):
-        nr = num_points(p.eta_r, p.lray_cells if p.lray_cells > 0 else p.N * math.sqrt(3.0))
+        diag = (2.0 if p.bc == BC_CORNER else 1.0) * p.N * math.sqrt(3.0)
+        nr = num_points(p.eta_r, p.lray_cells if p.lray_cells > 0 else diag)
         npix = 12 * p.nside * p.nside
         ba, be = np.zeros(npix * nr), np.zeros(npix * nr)
         bee = np.zeros(npix * nr) if self.use_e else None

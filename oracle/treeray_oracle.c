@@ -61,6 +61,16 @@
  *     conditions give; with N <= 2 points, or when the linear prescription
  *     makes a weight negative, the two-point W_f,3 is used (emission stays
  *     non-negative and both conditions still hold).
+ *  R12 boundaries (Sec. 2.8): periodic takes, for every node that does not
+ *     contain the target, the copy whose geometric centre is nearest to the
+ *     target centre, per axis, with the offset o in half cells wrapped into
+ *     [-N, N) (N finest cells per axis); the distance uses that copy's
+ *     centre of mass.  Corner of symmetry puts the corner at the grid's low
+ *     corner: the walk runs over the original and its 7 mirror images
+ *     (every subset of the axes mirrored through the corner planes), all
+ *     deposited onto the same rays; only the original can contain the
+ *     target, and the default maximum ray length becomes the diagonal of
+ *     the mirrored domain, 2 N sqrt3.
  */
 #include "treeray_oracle.h"
 
@@ -748,6 +758,7 @@ typedef struct {
     int64_t tx, ty, tz;       /* target corner, finest cells */
     int64_t ts;               /* target edge, finest cells */
     double cx, cy, cz;        /* target centre */
+    int32_t img;              /* corner of symmetry: mirrored axes (bit a: axis a) of this image */
     int32_t nr;
     double lray;
     double th_lim2, th_if2, th_src2;
@@ -756,6 +767,37 @@ typedef struct {
     int64_t* acc; int64_t cap; int64_t nacc;
     int64_t visited;
 } walk_ctx;
+
+/* Offset o = 2 (node geometric centre - target centre), in half cells, of
+ * the copy of the node that the boundary condition puts next to the target
+ * (R12), and the target centre to measure that copy's distance from in the
+ * node's own frame. */
+static void node_frame(const walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t iz,
+                       int64_t o[3], double tc[3])
+{
+    int64_t N = w->t->N, s = N >> level;
+    int64_t g2[3] = {2 * ix * s + s, 2 * iy * s + s, 2 * iz * s + s};
+    int64_t t2[3] = {2 * w->tx + w->ts, 2 * w->ty + w->ts, 2 * w->tz + w->ts};
+    double c[3] = {w->cx, w->cy, w->cz};
+    for (int a = 0; a < 3; ++a) {
+        if (w->p->bc == ORC_BC_CORNER && ((w->img >> a) & 1)) {
+            /* image mirrored in axis a: the node sits at -g, i.e. the
+             * original node seen from the mirrored target -t */
+            o[a] = -(g2[a] + t2[a]);
+            tc[a] = -c[a];
+        } else {
+            o[a] = g2[a] - t2[a];
+            tc[a] = c[a];
+            if (w->p->bc == ORC_BC_PERIODIC) {
+                int64_t k = 0;
+                if (o[a] >= N) k = -1;
+                else if (o[a] < -N) k = 1;
+                o[a] += 2 * N * k;             /* copy shifted by k N cells */
+                tc[a] -= (double)(k * N);
+            }
+        }
+    }
+}
 
 static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t iz,
                      const orc_node* nd, double d)
@@ -767,10 +809,10 @@ static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t
     if (nd->alpha == 0.0 && nd->eps == 0.0 && (!use_e || nd->e == 0.0)) return;
     if (d > w->lray) return;                       /* beyond the maximum ray length (R6) */
     int64_t s = (int64_t)(w->t->N >> level);
-    int64_t ox = 2 * ix * s + s - 2 * w->tx - w->ts;   /* 2 x (geometric centre - target centre) */
-    int64_t oy = 2 * iy * s + s - 2 * w->ty - w->ts;
-    int64_t oz = 2 * iz * s + s - 2 * w->tz - w->ts;
-    const orc_entry* ent = table_entry(p->nside, orc_table_key(ox, oy, oz, s));
+    int64_t o[3];
+    double tc[3];
+    node_frame(w, level, ix, iy, iz, o, tc);
+    const orc_entry* ent = table_entry(p->nside, orc_table_key(o[0], o[1], o[2], s));
     int32_t nr = w->nr;
     double h = (double)s;
     if (nd->alpha != 0.0) smooth_weights(p->kernel_alpha == ORC_K_WG, d, h, nr, p->eta_r, w->wa);
@@ -796,7 +838,8 @@ static void walk_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_
     int64_t s = (int64_t)(t->N >> level);
     int fl = node_flag(t, level, lidx(n, ix, iy, iz));
     w->visited++;
-    int contains = (w->tx >= ix * s && w->tx < ix * s + s) && (w->ty >= iy * s && w->ty < iy * s + s) &&
+    int contains = w->img == 0 &&
+                   (w->tx >= ix * s && w->tx < ix * s + s) && (w->ty >= iy * s && w->ty < iy * s + s) &&
                    (w->tz >= iz * s && w->tz < iz * s + s);
     if (contains) {
         if (fl == ORC_LEAF) return;                /* the target itself (R3) */
@@ -804,9 +847,12 @@ static void walk_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_
             walk_node(w, level + 1, 2 * ix + (ch & 1), 2 * iy + ((ch >> 1) & 1), 2 * iz + ((ch >> 2) & 1));
         return;
     }
-    double dx = w->cx - nd->cm[0];
-    double dy = w->cy - nd->cm[1];
-    double dz = w->cz - nd->cm[2];
+    int64_t o[3];
+    double tc[3];
+    node_frame(w, level, ix, iy, iz, o, tc);       /* the copy of the node next to the target (R12) */
+    double dx = tc[0] - nd->cm[0];
+    double dy = tc[1] - nd->cm[1];
+    double dz = tc[2] - nd->cm[2];
     double d2 = (dx * dx + dy * dy) + dz * dz;
     if (fl != ORC_LEAF) {
         double h2 = (double)s * (double)s;
@@ -823,7 +869,11 @@ static void walk_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_
     map_node(w, level, ix, iy, iz, nd, sqrt(d2));
 }
 
-static double lray_of(const orc_params* p) { return p->lray_cells > 0.0 ? p->lray_cells : (double)p->N * sqrt(3.0); }
+static double lray_of(const orc_params* p)
+{
+    if (p->lray_cells > 0.0) return p->lray_cells;
+    return (p->bc == ORC_BC_CORNER ? 2.0 : 1.0) * (double)p->N * sqrt(3.0);   /* R12 */
+}
 
 int64_t orc_walk_target(const orc_tree* t, const orc_params* p, int64_t target,
                         double* bins_alpha, double* bins_eps, double* bins_e,
@@ -855,7 +905,8 @@ int64_t orc_walk_target(const orc_tree* t, const orc_params* p, int64_t target,
     orc_tree tt = *t;
     if (!bins_e) tt.use_e = 0;
     w.t = &tt;
-    walk_node(&w, 0, 0, 0, 0);
+    int32_t n_img = p->bc == ORC_BC_CORNER ? 8 : 1;
+    for (w.img = 0; w.img < n_img; ++w.img) walk_node(&w, 0, 0, 0, 0);
     free(scratch);
     if (n_accepted) *n_accepted = w.nacc;
     return w.visited;

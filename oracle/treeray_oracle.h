@@ -37,7 +37,11 @@ typedef struct {
     int32_t zeta_g;       /* 1: apply the geometric correction (Eq. 16) */
     int32_t kernel_alpha; /* radial kernel for alpha and e: ORC_K_WP or ORC_K_WG */
     int32_t kernel_eps;   /* radial kernel for eps: ORC_KE_* */
+    int32_t bc;           /* boundary: ORC_BC_ISOLATED, ORC_BC_PERIODIC, ORC_BC_CORNER */
 } orc_params;
+
+/* boundary conditions of the walk (Sec. 2.8) */
+enum { ORC_BC_ISOLATED = 0, ORC_BC_PERIODIC = 1, ORC_BC_CORNER = 2 };
 
 /* kernel choices (App. A) */
 enum { ORC_K_WP = 0, ORC_K_WG = 1 };

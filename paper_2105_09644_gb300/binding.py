@@ -18,6 +18,7 @@ TR_OK, TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_ETIMEOUT, TR_EUNSUPPORTED, TR_EOVERFLO
 TR_FP64, TR_FP32_SWEEP64 = 0, 1
 TR_KERNEL_WP, TR_KERNEL_WG = 0, 1
 TR_EPS_WF3, TR_EPS_WF1, TR_EPS_WF2, TR_EPS_WF3N, TR_EPS_WP, TR_EPS_WG = range(6)
+TR_BC_ISOLATED, TR_BC_PERIODIC, TR_BC_CORNER = 0, 1, 2
 STATUS_NAMES = {0: "TR_OK", 1: "TR_EINVAL", 2: "TR_ENOMEM", 3: "TR_ECUDA", 4: "TR_ETIMEOUT",
                 5: "TR_EUNSUPPORTED", 6: "TR_EOVERFLOW"}
 
@@ -40,7 +41,8 @@ class Params(C.Structure):
                 ("nside", C.c_int32), ("eta_r", C.c_int32), ("L_ray_cm", C.c_double),
                 ("alpha_B", C.c_double), ("hnu", C.c_double), ("eps_lim", C.c_double),
                 ("delta_mode", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("zeta_g", C.c_int32), ("kernel_alpha", C.c_int32), ("kernel_eps", C.c_int32)]
+                ("zeta_g", C.c_int32), ("kernel_alpha", C.c_int32), ("kernel_eps", C.c_int32),
+                ("bc", C.c_int32)]
 
 
 class Grid(C.Structure):

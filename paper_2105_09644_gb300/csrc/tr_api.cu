@@ -58,7 +58,15 @@ tr_status check_params(const tr_params* p) {
         return set_error(TR_EINVAL, "kernel_alpha must be TR_KERNEL_WP or TR_KERNEL_WG (got %d)", p->kernel_alpha);
     if (p->kernel_eps < TR_EPS_WF3 || p->kernel_eps > TR_EPS_WG)
         return set_error(TR_EINVAL, "kernel_eps must be one of tr_eps_kernel (got %d)", p->kernel_eps);
+    if (p->bc < TR_BC_ISOLATED || p->bc > TR_BC_CORNER)
+        return set_error(TR_EINVAL, "bc must be one of tr_bc (got %d)", p->bc);
     return TR_OK;
+}
+
+// default maximum ray length in cells: the domain diagonal (of the mirrored
+// domain under the corner-of-symmetry boundary)
+double default_lray(int N, const tr_params* p) {
+    return (p->bc == TR_BC_CORNER ? 2.0 : 1.0) * (double)N * std::sqrt(3.0);
 }
 
 tr_status check_grid(const tr_grid* g, const tr_sources* s) {
@@ -113,7 +121,7 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
     const int N = g->N;
     int L = 0;
     while ((1 << L) < N) ++L;
-    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx : (double)N * std::sqrt(3.0);
+    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx : default_lray(N, p);
     const int nr = p->eta_r * (int)std::floor(std::sqrt(2.0 * lray)) + 1;      // Eq. 5
     if (nr > MAX_NR) return set_error(TR_EUNSUPPORTED, "N_R = %d exceeds %d evaluation points", nr, MAX_NR);
     if (nr < 3) return set_error(TR_EINVAL, "L_ray too short: N_R = %d", nr);
@@ -223,7 +231,7 @@ tr_status build_amr(const tr_amr_grid* g, const tr_sources* s, const tr_params* 
     int dev = 0;
     if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice")) != TR_OK) return rc;
     const int N = g->N_base << g->max_level;
-    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx_fine : (double)N * std::sqrt(3.0);
+    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx_fine : default_lray(N, p);
     const int nr = p->eta_r * (int)std::floor(std::sqrt(2.0 * lray)) + 1;      // Eq. 5
     if (nr > MAX_NR) return set_error(TR_EUNSUPPORTED, "N_R = %d exceeds %d evaluation points", nr, MAX_NR);
     if (nr < 3) return set_error(TR_EINVAL, "L_ray too short: N_R = %d", nr);
@@ -357,6 +365,7 @@ void tr_params_default(tr_params* p) {
     p->zeta_g = 1;
     p->kernel_alpha = TR_KERNEL_WP;
     p->kernel_eps = TR_EPS_WF3;
+    p->bc = TR_BC_ISOLATED;
 }
 
 const char* tr_last_error(void) { return g_err; }

@@ -99,7 +99,9 @@ extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, con
     const int N = g->N;
     int L = 0;
     while ((1 << L) < N) ++L;
-    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx : (double)N * std::sqrt(3.0);
+    if (p->bc < TR_BC_ISOLATED || p->bc > TR_BC_CORNER) return set_error(TR_EINVAL, "bc must be one of tr_bc");
+    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx
+                                          : (p->bc == TR_BC_CORNER ? 2.0 : 1.0) * (double)N * std::sqrt(3.0);
     const int nr = p->eta_r * (int)std::floor(std::sqrt(2.0 * lray)) + 1;     // Eq. 5
     if (nr > MAX_NR || nr < 3) return set_error(TR_EUNSUPPORTED, "N_R = %d outside [3, %d]", nr, MAX_NR);
 

@@ -57,6 +57,7 @@ struct WalkArgs {
     const uint32_t* blk_order;              // AMR tree: blocks in walk order
     int64_t n_cells;                        // valid target indices are [0, n_cells)
     int kern_a, kern_e;                     // tr_kernel (alpha, e) and tr_eps_kernel (eps)
+    int bc;                                 // tr_bc of the walk
     int64_t n_targets;
     double Fconv, Econv;                    // scaled flux -> CGS flux / energy density
     double* F;
@@ -105,6 +106,26 @@ __device__ __forceinline__ T wg_kernel(T x) {
 template <typename T>
 __device__ __forceinline__ T radial_w(T dist, T hpar, int gauss) {
     return gauss ? wg_kernel<T>(dist / hpar) : wp_kernel<T>(dist * hpar);
+}
+
+// Stack entry standing for "evaluate the root node" (real entries hold a
+// level <= 9 in their top 5 bits, so this value never occurs as one).
+constexpr uint32_t ROOT_EVAL = 0xffffffffu;
+
+// One axis of the node copy the boundary condition puts next to the target
+// (Sec. 2.8): g2, t2 = twice the node's and the target's centre (finest
+// cells).  Corner of symmetry, axis mirrored: the node seen from the
+// mirrored target.  Periodic: the nearest copy, offset wrapped into [-N, N)
+// half cells.
+template <typename T>
+__device__ __forceinline__ void bc_frame(int bc, int mirrored, int N, int g2, int t2, T p, int& o, T& q) {
+    if (bc == TR_BC_CORNER && mirrored) { o = -(g2 + t2); q = -p; return; }
+    o = g2 - t2;
+    q = p;
+    if (bc == TR_BC_PERIODIC) {
+        if (o >= N) { o -= 2 * N; q += (T)N; }
+        else if (o < -N) { o += 2 * N; q -= (T)N; }
+    }
 }
 
 __device__ __forceinline__ int face_bin(int x, int A) {
@@ -735,8 +756,9 @@ __device__ __forceinline__ void flush_counters(const WalkArgs& a, unsigned long 
 // jobs (a job = one tree and a range or list of its cells).  Several trees in
 // one launch is how independent requests are batched together.  Each step
 // pops NT/8 opened nodes and evaluates their NT children, one per thread.
-// VAR: the kernel choices other than W_p / W_f,3 are compiled in (a
-// separate instantiation, so that the default walk keeps its registers).
+// VAR: the kernel choices other than W_p / W_f,3 and the periodic and
+// corner-of-symmetry boundaries are compiled in (a separate instantiation,
+// so that the default walk keeps its registers).
 template <int MODE, bool DUMP, int NT, bool VAR>
 __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
                                             int n_jobs, unsigned int* counter) {
@@ -847,6 +869,15 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
         int top = 1, max_top = 1;
         bool overflow = false;
         __syncthreads();
+        // corner of symmetry: the original and its 7 mirror images (bit k of
+        // img mirrors axis k through the low corner), all onto the same rays
+        const int n_img = (VAR && a.bc == TR_BC_CORNER) ? 8 : 1;
+        for (int img = 0; img < n_img && !overflow; ++img) {
+        if (img > 0) {
+            if (tid == 0) stack[0] = ROOT_EVAL;
+            top = 1;
+            __syncthreads();                                     // the image's root visible
+        }
         while (top > 0) {
             const int np = min(P, top);
             const int pi = tid >> 3, c = tid & 7;
@@ -858,14 +889,16 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             uint32_t mort = 0;
             RadialSpread<MODE> node;
             bool spread = false;
-            if (pi < np) {
+            // ROOT_EVAL: the root itself is evaluated (a mirror image does not
+            // contain the target, so its root is subject to the MACs)
+            if (pi < np && (!VAR || pe != ROOT_EVAL || c == 0)) {
                 ++n_vis;
-                lev = (int)(pe >> 27) + 1;
-                mort = ((pe & 0x7ffffffu) << 3) | (uint32_t)c;
+                lev = (VAR && pe == ROOT_EVAL) ? 0 : (int)(pe >> 27) + 1;
+                mort = (VAR && pe == ROOT_EVAL) ? 0u : (((pe & 0x7ffffffu) << 3) | (uint32_t)c);
                 const int s = N >> lev;
                 const int cx = (int)compact3(mort) * s, cy = (int)compact3(mort >> 1) * s,
                           cz = (int)compact3(mort >> 2) * s;
-                const bool contains = (tx >= cx && tx < cx + s) && (ty >= cy && ty < cy + s) &&
+                const bool contains = img == 0 && (tx >= cx && tx < cx + s) && (ty >= cy && ty < cy + s) &&
                                       (tz >= cz && tz < cz + s);
                 const int64_t nid = level_offset(lev) + mort;
                 const bool leaf = a.flags ? (__ldg(a.flags + nid) == NODE_LEAF) : (lev == L);
@@ -874,7 +907,17 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                 } else {
                     real cm[3], m, qv[3], mion;
                     load_node<MODE>(a.nodes, nid, cm, m, qv, mion);
-                    const real d2 = dist2(px, py, pz, cm);
+                    // offset o = 2 (node centre - target centre) in half cells of the node
+                    // copy that the boundary puts next to the target, and the target
+                    // centre to measure that copy's distance from in the node's frame
+                    int ox = 2 * cx + s - 2 * tx - ts, oy = 2 * cy + s - 2 * ty - ts, oz = 2 * cz + s - 2 * tz - ts;
+                    real qx = px, qy = py, qz = pz;
+                    if (VAR && a.bc != TR_BC_ISOLATED) {
+                        bc_frame<real>(a.bc, img & 1, N, 2 * cx + s, 2 * tx + ts, px, ox, qx);
+                        bc_frame<real>(a.bc, (img >> 1) & 1, N, 2 * cy + s, 2 * ty + ts, py, oy, qy);
+                        bc_frame<real>(a.bc, (img >> 2) & 1, N, 2 * cz + s, 2 * tz + ts, pz, oz, qz);
+                    }
+                    const real d2 = dist2(qx, qy, qz, cm);
                     const real h2 = (real)s * (real)s;
                     if (!leaf && must_open(h2, d2, m, mion, qv[1], a)) {
                         action = 1;
@@ -884,8 +927,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                         const bool in_reach = (MODE == 0) ? ((double)d <= a.lray) : ((float)d <= a.lrayf);
                         const bool has_ae = qv[0] != real(0) || (a.use_e && qv[2] != real(0));
                         if (in_reach && (has_ae || qv[1] != real(0))) {
-                            const int key = table_key(2 * cx + s - 2 * tx - ts, 2 * cy + s - 2 * ty - ts,
-                                                      2 * cz + s - 2 * tz - ts, s);
+                            const int key = table_key(ox, oy, oz, s);
                             const uint2 hd = __ldg(a.hdr + key);
                             ne = (int)hd.y;
                             n_ent += ne;
@@ -969,6 +1011,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             top += ototal;
             max_top = max(max_top, top);
         }
+        }                                                        // images
         __syncthreads();                                         // all spreads done
         // own emission of the target (Sec. 2.5 footnote: target sphere of
         // radius r_tp = half the cell edge)
@@ -1080,6 +1123,7 @@ WalkArgs make_args(const tr_tree* t) {
     a.n_cells = t->n_cells;
     a.kern_a = t->p.kernel_alpha;
     a.kern_e = t->p.kernel_eps;
+    a.bc = t->p.bc;
     a.flags = t->flags;
     a.blk = t->blk;
     a.blk_order = t->blk_order;
@@ -1156,7 +1200,9 @@ tr_status launch_jobs(int mode, bool dump, bool var, size_t smem, const WalkArgs
                : launch_jobs_v<false>(mode, dump, wide, smem, jobs, job_end, n_jobs, total, counter, st);
 }
 
-bool uses_variants(const tr_tree* t) { return t->p.kernel_alpha != TR_KERNEL_WP || t->p.kernel_eps != TR_EPS_WF3; }
+bool uses_variants(const tr_tree* t) {
+    return t->p.kernel_alpha != TR_KERNEL_WP || t->p.kernel_eps != TR_EPS_WF3 || t->p.bc != TR_BC_ISOLATED;
+}
 
 }  // namespace
 
