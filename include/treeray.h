@@ -267,6 +267,19 @@ tr_status tr_delta(const double* e_new, const double* e_old, int64_t n, int32_t 
 tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, const tr_params* p,
                            double* F_out, double* e_out, uint8_t* ion_out, tr_stream stream);
 
+/* Column-density maps (cdMaps, the TreeRay/OpticalDepth quantity that the
+ * paper's ray-arrays include, Sec. 2.2): the same walk and MACs as
+ * tr_walk_sweep over a built tree, but each accepted node adds to direction
+ * k of the target its mass times its volume fraction in ray k over the
+ * ray's cross-section at the node, w_k m / (Omega d^2), Omega = 4 pi /
+ * N_PIX; no radial points, no sweep, no maximum ray length, and the target
+ * cell itself left out.  out: device [n_targets][N_PIX] hydrogen column
+ * densities, cm^-2 (targets as for tr_walk_map; NULL with n_targets = the
+ * cell count gives row c for cell c).  Synchronises `stream`.
+ * Errors: TR_EINVAL, TR_ECUDA, TR_EOVERFLOW. */
+tr_status tr_column_density(const tr_tree* t, const int64_t* targets, int64_t n_targets, double* out,
+                            tr_stream stream);
+
 /* ---- inspection (parity tests) -------------------------------------- */
 
 /* Sizes of a tree: node count, levels (log2 N + 1), N_R, N_PIX. Host outputs. */

@@ -108,6 +108,7 @@ def lib():
             L.orc_walk_target.restype = C.c_int64
             L.orc_walk_target.argtypes = [C.c_void_p, C.POINTER(Params), C.c_int64, _D, _D, _D,
                                           _I64, C.c_int64, _I64]
+            L.orc_column_density.argtypes = [C.c_void_p, C.POINTER(Params), C.c_int64, _D]
             L.orc_solve_pass.restype = C.c_int32
             L.orc_solve_pass.argtypes = [C.c_void_p, C.POINTER(Params), _I64, C.c_int64, _D, _D, _U8]
             L.orc_solve.restype = C.c_int32
@@ -283,6 +284,12 @@ class Tree:
         return dict(visited=int(visited), accepted=acc[:min(n, cap)].copy(), n_accepted=n,
                     alpha=ba.reshape(npix, nr), eps=be.reshape(npix, nr),
                     e=None if bee is None else bee.reshape(npix, nr))
+
+    def column_density(self, p: Params, target: int) -> np.ndarray:
+        """cdMaps of one target: N_PIX column densities in cm^-2."""
+        out = np.zeros(12 * p.nside * p.nside)
+        lib().orc_column_density(self.h, C.byref(p), int(target), _p(out))
+        return out
 
     def solve_pass(self, p: Params, targets=None):
         if targets is None:

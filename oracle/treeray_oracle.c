@@ -71,6 +71,13 @@
  *     deposited onto the same rays; only the original can contain the
  *     target, and the default maximum ray length becomes the diagonal of
  *     the mirrored domain, 2 N sqrt3.
+ *  R13 column-density maps (cdMaps, Sec. 2.2; defined in Paper I, which is
+ *     not given): the same walk, and each accepted node adds to direction k
+ *     its mass times its volume fraction in cone k over the cone's
+ *     cross-section at the node, w_k m / (Omega d^2) with Omega = 4 pi /
+ *     N_PIX, so that sum_k Omega N_k = sum_n m_n / d_n^2.  All accepted
+ *     nodes count (a map has no radial points, so no maximum ray length);
+ *     the target cell itself is left out.
  */
 #include "treeray_oracle.h"
 
@@ -766,6 +773,7 @@ typedef struct {
     double *wa, *we, *wee;
     int64_t* acc; int64_t cap; int64_t nacc;
     int64_t visited;
+    double* cd;               /* column-density map of the target (R13), or NULL */
 } walk_ctx;
 
 /* Offset o = 2 (node geometric centre - target centre), in half cells, of
@@ -805,6 +813,18 @@ static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t
     const orc_params* p = w->p;
     if (w->acc) { if (w->nacc < w->cap) w->acc[w->nacc] = canonical_id(level, ix, iy, iz); }
     w->nacc++;
+    if (w->cd) {                                   /* column-density map (R13) */
+        if (nd->m == 0.0) return;
+        int64_t o[3];
+        double tc[3];
+        node_frame(w, level, ix, iy, iz, o, tc);
+        const orc_entry* ent = table_entry(p->nside, orc_table_key(o[0], o[1], o[2], (int64_t)(w->t->N >> level)));
+        double omega = 4.0 * ORC_PI / (double)(12 * (int64_t)p->nside * p->nside);
+        const double inv_m3 = 1.0 / (double)(ORC_TM * ORC_TM * ORC_TM);
+        for (int32_t j = 0; j < ent->n; ++j)
+            w->cd[ent->pix[j]] += ((double)ent->cnt[j] * inv_m3) * nd->m / (omega * (d * d));
+        return;
+    }
     int use_e = w->t->use_e;
     if (nd->alpha == 0.0 && nd->eps == 0.0 && (!use_e || nd->e == 0.0)) return;
     if (d > w->lray) return;                       /* beyond the maximum ray length (R6) */
@@ -910,6 +930,31 @@ int64_t orc_walk_target(const orc_tree* t, const orc_params* p, int64_t target,
     free(scratch);
     if (n_accepted) *n_accepted = w.nacc;
     return w.visited;
+}
+
+void orc_column_density(const orc_tree* t, const orc_params* p, int64_t target, double* out)
+{   /* cdMaps (R13): N_PIX column densities of one target, cm^-2 */
+    walk_ctx w;
+    memset(&w, 0, sizeof w);
+    w.t = t; w.p = p;
+    int32_t tl;
+    int64_t p3[3], edge;
+    target_geom(t, target, &tl, p3, &edge);
+    w.tx = p3[0] * edge; w.ty = p3[1] * edge; w.tz = p3[2] * edge; w.ts = edge;
+    w.cx = (double)w.tx + 0.5 * (double)edge;
+    w.cy = (double)w.ty + 0.5 * (double)edge;
+    w.cz = (double)w.tz + 0.5 * (double)edge;
+    w.lray = lray_of(p);
+    w.th_lim2 = p->theta_lim * p->theta_lim;
+    w.th_if2 = p->theta_if * p->theta_if;
+    w.th_src2 = p->theta_src * p->theta_src;
+    int64_t npix = 12 * (int64_t)p->nside * p->nside;
+    for (int64_t k = 0; k < npix; ++k) out[k] = 0.0;
+    w.cd = out;
+    int32_t n_img = p->bc == ORC_BC_CORNER ? 8 : 1;
+    for (w.img = 0; w.img < n_img; ++w.img) walk_node(&w, 0, 0, 0, 0);
+    /* mass n_H cells^3 over cells^2 -> n_H cells -> cm^-2 */
+    for (int64_t k = 0; k < npix; ++k) out[k] *= t->dx_cm;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -106,6 +106,9 @@ int64_t orc_walk_target(const orc_tree* t, const orc_params* p, int64_t target,
 
 /* one pass (walk, map, sweep) over a list of targets (NULL = all cells).
  * F in photons s^-1 cm^-2, e in erg cm^-3, ion = 1 where F > 0. */
+/* column-density map of one target (cdMaps): N_PIX values, cm^-2 */
+void orc_column_density(const orc_tree* t, const orc_params* p, int64_t target, double* out);
+
 int32_t orc_solve_pass(const orc_tree* t, const orc_params* p, const int64_t* targets,
                        int64_t n_targets, double* F_out, double* e_out, uint8_t* ion_out);
 

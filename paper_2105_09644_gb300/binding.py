@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_EINVAL", 2: "TR_ENOMEM", 3: "TR_ECUDA", 4: "T
 
 # every symbol include/treeray.h declares
 EXPORTED = ["tr_params_default", "tr_build_tree", "tr_build_tree_amr", "tr_tree_cells", "tr_tree_flags",
-            "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve",
+            "tr_walk_map", "tr_ray_sweep", "tr_walk_sweep", "tr_solve", "tr_column_density",
             "tr_tree_stats", "tr_solve_noalloc", "tr_delta", "tr_walk_sweep_batch",
             "tr_tree_info", "tr_tree_nodes", "tr_rays_info", "tr_rays_export", "tr_table_info",
             "tr_table_export", "tr_tree_free", "tr_rays_free", "tr_last_error"]
@@ -80,6 +80,7 @@ def load():
     L.tr_tree_cells.argtypes = [vp, C.POINTER(i64)]
     L.tr_tree_flags.argtypes = [vp, vp, vp]
     L.tr_walk_map.argtypes = [vp, vp, i64, C.POINTER(vp), vp]
+    L.tr_column_density.argtypes = [vp, vp, i64, vp, vp]
     L.tr_ray_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_walk_sweep.argtypes = [vp, vp, vp, vp, vp]
     L.tr_tree_stats.argtypes = [vp, C.POINTER(i64)]
@@ -237,6 +238,18 @@ def tr_walk_map(tree: Tree, targets=None, n_targets: int | None = None, stream=N
         n = int(n_targets)
     check(load().tr_walk_map(tree.h, _ptr(targets), n, C.byref(rays.h), _stream(stream)))
     return rays
+
+
+def tr_column_density(tree: Tree, out, targets=None, stream=None):
+    """Column-density maps: out is a device float64 tensor [n_targets, N_PIX]
+    (n_targets = the cell count when targets is None)."""
+    if targets is not None:
+        assert targets.is_cuda and targets.dtype.itemsize == 8 and targets.is_contiguous()
+        n = int(targets.numel())
+    else:
+        n = tr_tree_cells(tree)
+    assert out.is_cuda and out.dtype.itemsize == 8 and out.is_contiguous() and out.numel() >= n * tree.info()["npix"]
+    check(load().tr_column_density(tree.h, _ptr(targets), n, _ptr(out), _stream(stream)))
 
 
 def tr_ray_sweep(rays: Rays, F=None, e=None, ion=None, stream=None):

@@ -493,6 +493,18 @@ tr_status tr_walk_sweep_batch(const tr_tree* const* trees, const int64_t* first,
     return TR_OK;
 }
 
+tr_status tr_column_density(const tr_tree* t, const int64_t* targets, int64_t n_targets, double* out,
+                            tr_stream stream) {
+    g_err[0] = '\0';
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!t || !out) return set_error(TR_EINVAL, "tree or output is NULL");
+    if (n_targets < 0 || n_targets > t->n_cells) return set_error(TR_EINVAL, "n_targets out of range");
+    if (!targets && n_targets != t->n_cells) return set_error(TR_EINVAL, "targets NULL requires n_targets = the cell count");
+    tr_status rc = cd_run(t, targets, n_targets, out, st);
+    if (rc == TR_OK) rc = read_status(t, st);
+    return rc;
+}
+
 tr_status tr_tree_stats(const tr_tree* t, int64_t* out4) {
     g_err[0] = '\0';
     if (!t || !out4) return set_error(TR_EINVAL, "tree or output is NULL");

@@ -171,6 +171,8 @@ struct WalkOut {
 tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, bool dump,
                    const WalkOut& out, cudaStream_t st);
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st);
+// column-density maps of targets (NULL: cells 0 .. n_targets-1), out [target][N_PIX]
+tr_status cd_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, double* out, cudaStream_t st);
 size_t walk_job_bytes(int n_jobs);
 tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, const int64_t* count, int n,
                          double* const* F, double* const* e, uint8_t* const* ion, void* jobbuf, unsigned int* counter,

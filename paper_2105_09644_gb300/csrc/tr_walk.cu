@@ -58,6 +58,9 @@ struct WalkArgs {
     int64_t n_cells;                        // valid target indices are [0, n_cells)
     int kern_a, kern_e;                     // tr_kernel (alpha, e) and tr_eps_kernel (eps)
     int bc;                                 // tr_bc of the walk
+    double* cd_out;                         // column-density maps: [target][N_PIX], cm^-2
+    double cd_conv;                         // n_H cells -> cm^-2 (the cell edge dx)
+    double cd_omega;                        // 4 pi / N_PIX
     int64_t n_targets;
     double Fconv, Econv;                    // scaled flux -> CGS flux / energy density
     double* F;
@@ -759,11 +762,29 @@ __device__ __forceinline__ void flush_counters(const WalkArgs& a, unsigned long 
 // VAR: the kernel choices other than W_p / W_f,3 and the periodic and
 // corner-of-symmetry boundaries are compiled in (a separate instantiation,
 // so that the default walk keeps its registers).
-template <int MODE, bool DUMP, int NT, bool VAR>
+// OUT: OUT_FUSED walk + map + sweep; OUT_DUMP keeps the raw bins and
+// accepted ids; OUT_CD column-density maps (no radial points, no sweep).
+constexpr int OUT_FUSED = 0, OUT_DUMP = 1, OUT_CD = 2;
+
+// Column-density map deposit of an accepted node (cdMaps): each table entry
+// (ray k, volume fraction w_k) adds w_k m / (Omega d^2).
+template <int MODE>
+__device__ __forceinline__ void deposit_cd(const WalkArgs& a, double* bins, uint32_t off, int ne,
+                                           typename Prec<MODE>::real m, typename Prec<MODE>::real d) {
+    const double md = (double)m / (a.cd_omega * ((double)d * (double)d));
+    const double inv_m3 = 1.0 / (double)(TM * TM * TM);
+    for (int k = 0; k < ne; ++k) {
+        const uint32_t en = __ldg(a.tent + off + k);
+        atomicAdd(bins + (en >> 16), ((double)(en & 0xffffu) * inv_m3) * md);
+    }
+}
+
+template <int MODE, int OUT, int NT, bool VAR>
 __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
                                             int n_jobs, unsigned int* counter) {
     using real = typename Prec<MODE>::real;
     constexpr int NW = NT / 32, P = NT / 8;
+    constexpr bool DUMP = OUT == OUT_DUMP, CD = OUT == OUT_CD;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_wcnt[NW], s_bcnt[NW], s_pcnt[NW];
     __shared__ double s_red[NW];
@@ -810,7 +831,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             for (int k = tid; k < (int)(sizeof(WalkArgs) / sizeof(int)); k += NT) dst[k] = src[k];
             __syncthreads();
             cur = j;
-            nr = a.nr; nbins = a.npix * nr; nq = a.use_e ? 3 : 2; N = a.N; L = a.L;
+            nr = a.nr; nbins = CD ? a.npix : a.npix * nr; nq = CD ? 1 : (a.use_e ? 3 : 2); N = a.N; L = a.L;
             bins_a = reinterpret_cast<double*>(smem);
             bins_eps = bins_a + nbins;
             bins_e = a.use_e ? bins_eps + nbins : nullptr;
@@ -921,6 +942,13 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                     const real h2 = (real)s * (real)s;
                     if (!leaf && must_open(h2, d2, m, mion, qv[1], a)) {
                         action = 1;
+                    } else if (CD) {
+                        action = 2;
+                        if (m > real(0)) {
+                            const uint2 hd = __ldg(a.hdr + table_key(ox, oy, oz, s));
+                            n_ent += hd.y;
+                            deposit_cd<MODE>(a, bins_a, hd.x, (int)hd.y, m, sqrt(d2));
+                        }
                     } else {
                         action = 2;
                         const real d = sqrt(d2);
@@ -1013,6 +1041,16 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
         }
         }                                                        // images
         __syncthreads();                                         // all spreads done
+        if (CD) {
+            if (tid == 0) atomicMax(a.status + 1, max_top);
+            if (overflow) {
+                if (tid == 0) atomicAdd(a.status, 1);
+                continue;
+            }
+            double* out = a.cd_out + (size_t)(a.targets ? q : cell) * a.npix;
+            for (int k = tid; k < a.npix; k += NT) out[k] = bins_a[k] * a.cd_conv;
+            continue;
+        }
         // own emission of the target (Sec. 2.5 footnote: target sphere of
         // radius r_tp = half the cell edge)
         real cmt[3], mt, qt[3], miont;
@@ -1165,7 +1203,8 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const i
 
 bool wide_ctas(int mode, size_t smem) {
     int per_sm = 0;
-    const void* k = mode == 0 ? (const void*)k_walk<0, false, WALK_NT, false> : (const void*)k_walk<1, false, WALK_NT, false>;
+    const void* k = mode == 0 ? (const void*)k_walk<0, OUT_FUSED, WALK_NT, false>
+                              : (const void*)k_walk<1, OUT_FUSED, WALK_NT, false>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WALK_NT, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -1175,29 +1214,35 @@ bool wide_ctas(int mode, size_t smem) {
 }
 
 template <bool VAR>
-tr_status launch_jobs_v(int mode, bool dump, bool wide, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
+tr_status launch_jobs_v(int mode, int out, bool wide, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
                         int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
     constexpr int W0 = WALK_NT_WIDE_F64, W1 = WALK_NT_WIDE_F32, T = WALK_NT;
+    constexpr int F = OUT_FUSED, D = OUT_DUMP, C = OUT_CD;
+    if (out == C)                                                // N_PIX bins only: never wide
+        return mode == 0 ? launch_persistent<T>(k_walk<0, C, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                         : launch_persistent<T>(k_walk<1, C, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    const bool dump = out == D;
     if (wide) {
         if (mode == 0)
-            return dump ? launch_persistent<W0>(k_walk<0, true, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                        : launch_persistent<W0>(k_walk<0, false, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-        return dump ? launch_persistent<W1>(k_walk<1, true, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent<W1>(k_walk<1, false, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+            return dump ? launch_persistent<W0>(k_walk<0, D, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                        : launch_persistent<W0>(k_walk<0, F, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+        return dump ? launch_persistent<W1>(k_walk<1, D, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent<W1>(k_walk<1, F, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
     }
     if (mode == 0)
-        return dump ? launch_persistent<T>(k_walk<0, true, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent<T>(k_walk<0, false, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-    return dump ? launch_persistent<T>(k_walk<1, true, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                : launch_persistent<T>(k_walk<1, false, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+        return dump ? launch_persistent<T>(k_walk<0, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                    : launch_persistent<T>(k_walk<0, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    return dump ? launch_persistent<T>(k_walk<1, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                : launch_persistent<T>(k_walk<1, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
 }
 
-// var: some job uses a kernel choice other than W_p / W_f,3
-tr_status launch_jobs(int mode, bool dump, bool var, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
+// var: some job uses a kernel choice other than W_p / W_f,3 or a boundary
+// other than isolated
+tr_status launch_jobs(int mode, int out, bool var, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
                       int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
-    const bool wide = wide_ctas(mode, smem);
-    return var ? launch_jobs_v<true>(mode, dump, wide, smem, jobs, job_end, n_jobs, total, counter, st)
-               : launch_jobs_v<false>(mode, dump, wide, smem, jobs, job_end, n_jobs, total, counter, st);
+    const bool wide = out != OUT_CD && wide_ctas(mode, smem);
+    return var ? launch_jobs_v<true>(mode, out, wide, smem, jobs, job_end, n_jobs, total, counter, st)
+               : launch_jobs_v<false>(mode, out, wide, smem, jobs, job_end, n_jobs, total, counter, st);
 }
 
 bool uses_variants(const tr_tree* t) {
@@ -1230,7 +1275,30 @@ tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, 
     if (s != TR_OK || n_targets <= 0) return s;
     const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(t->jobbuf);
     const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<const unsigned char*>(t->jobbuf) + sizeof(WalkArgs));
-    return launch_jobs(t->mode, dump, uses_variants(t), walk_smem(t), jobs, job_end, 1, n_targets, t->counter, st);
+    return launch_jobs(t->mode, dump ? OUT_DUMP : OUT_FUSED, uses_variants(t), walk_smem(t), jobs, job_end, 1, n_targets,
+                       t->counter, st);
+}
+
+tr_status cd_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, double* out, cudaStream_t st) {
+    WalkArgs a = make_args(t);
+    a.targets = targets;
+    a.first = 0;
+    a.n_targets = n_targets;
+    a.cd_out = out;
+    a.cd_conv = t->dx;
+    a.cd_omega = 4.0 * PI_D / (double)t->npix;
+    unsigned char host[sizeof(WalkArgs) + sizeof(int64_t)];
+    memcpy(host, &a, sizeof(WalkArgs));
+    memcpy(host + sizeof(WalkArgs), &n_targets, sizeof(int64_t));
+    tr_status s = cuda_check(cudaMemsetAsync(t->status, 0, 4 * sizeof(int32_t), st), "status reset");
+    if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
+    if (s == TR_OK) s = cuda_check(cudaMemcpyAsync(t->jobbuf, host, sizeof host, cudaMemcpyHostToDevice, st), "job copy");
+    if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "job copy");
+    if (s != TR_OK || n_targets <= 0) return s;
+    const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(t->jobbuf);
+    const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<const unsigned char*>(t->jobbuf) + sizeof(WalkArgs));
+    const size_t smem = (size_t)t->npix * 8 + (size_t)STACK_CAP * 4;
+    return launch_jobs(t->mode, OUT_CD, uses_variants(t), smem, jobs, job_end, 1, n_targets, t->counter, st);
 }
 
 tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, const int64_t* count, int n,
@@ -1262,7 +1330,7 @@ tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, cons
     if (s != TR_OK || total == 0) return s;
     const WalkArgs* jobs = reinterpret_cast<const WalkArgs*>(jobbuf);
     const int64_t* job_end = reinterpret_cast<const int64_t*>(reinterpret_cast<unsigned char*>(jobbuf) + (size_t)n * sizeof(WalkArgs));
-    return launch_jobs(trees[0]->mode, false, var, smem, jobs, job_end, n, total, counter, st);
+    return launch_jobs(trees[0]->mode, OUT_FUSED, var, smem, jobs, job_end, n, total, counter, st);
 }
 
 tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaStream_t st) {
