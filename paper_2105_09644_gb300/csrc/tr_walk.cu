@@ -603,8 +603,8 @@ __device__ __forceinline__ float phi_f(const float2 E, const float2 Lr) {  // E 
 // lane gl owns the ray's source points j with j % SG == gl and keeps their
 // budgets and losses; the total flux of each segment (for zeta_s, zeta_d) is
 // summed over the group with shuffles.  All lanes of the group return F_0.
-constexpr int SG = 4;
-constexpr uint64_t SG_PATTERN = 0x1111111111111111ull;   // bits j with j % 4 == 0
+constexpr int SG = 2;
+constexpr uint64_t SG_PATTERN = 0x5555555555555555ull;   // bits j with j % 2 == 0
 
 __device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* be, const double* bee,
                                   const Scales& sc, int gl, unsigned gmask) {
