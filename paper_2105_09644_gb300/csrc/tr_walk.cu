@@ -35,6 +35,8 @@ struct WalkArgs {
     const void* nodes;
     int N, L, nr, npix, eta, nside, use_e, stack_cap;
     double th_lim2, th_if2, th_src2, lray;
+    double r_coef;                          // r_i = i^2 r_coef cells, r_coef = 1 / (2 eta^2) (Eq. 4)
+    float r_coeff;                          // the same (a power of two: exact in FP32)
     float th_lim2f, th_if2f, th_src2f, lrayf;
     const uint32_t* toff;
     const uint32_t* tent;
@@ -89,9 +91,16 @@ __device__ __forceinline__ T wp_kernel(T x) {
     const T a1 = T(1.21), a2 = T(-6.35), A = T(4.08), M = T(1.184);
     const T s3h = T(0.86602540378443864676);
     const T c2 = T(2.0) * A * (T(2.0) + T(1.73205080756887729353)) - T(0.5) * a2;
-    if (x < T(0.5)) return M + x * x * (a1 * x - (T(0.5) * a1 + T(4.0) * (M - A)));
-    if (x < s3h) { T t = x - s3h; return t * t * (a2 * x + c2); }
-    return T(0);
+    if constexpr (sizeof(T) == 8) {          // FP64: evaluate only the branch needed
+        if (x < T(0.5)) return M + x * x * (a1 * x - (T(0.5) * a1 + T(4.0) * (M - A)));
+        if (x < s3h) { T t = x - s3h; return t * t * (a2 * x + c2); }
+        return T(0);
+    } else {                                 // FP32: both branches and a select (lanes of a warp
+        const T inner = M + x * x * (a1 * x - (T(0.5) * a1 + T(4.0) * (M - A)));   // sit on either side)
+        const T t = x - s3h;
+        const T outer = t * t * (a2 * x + c2);
+        return x < T(0.5) ? inner : (x < s3h ? outer : T(0));
+    }
 }
 
 // W_g of App. A (Eq. A1): exp(-x^2), truncated at sqrt3/2.
@@ -271,13 +280,21 @@ struct RadialSpread {
 
 constexpr int MAXW = 12;                    // W_p values kept per node (longer supports recompute)
 
+// r_i of Eq. 4: in FP32 from its index, i^2 times a power of two (exact, no
+// load); in FP64 from the table (an FP64 multiply costs more than the load)
+template <typename T>
+__device__ __forceinline__ T radius_at(int i, T coef, const double* tab) {
+    if constexpr (sizeof(T) == 8) return __ldg(tab + i);
+    else return (T)(i * i) * coef;
+}
+
 template <int MODE>
 __device__ __forceinline__ typename Prec<MODE>::real spread_weight(const RadialSpread<MODE>& n, int j,
-                                                                 const typename Prec<MODE>::real* r,
+                                                                 typename Prec<MODE>::real rcoef, const double* rtab,
                                                                  const typename Prec<MODE>::real* wts, int gauss) {
     using real = typename Prec<MODE>::real;
     if (n.kind == 3) return wts[n.src * MAXW + n.woff + j] * n.b;
-    if (n.kind == 0) return radial_w<real>(fabs(r[n.lo + j] - n.d), n.a, gauss) * n.b;
+    if (n.kind == 0) return radial_w<real>(fabs(radius_at<real>(n.lo + j, rcoef, rtab) - n.d), n.a, gauss) * n.b;
     if (n.kind == 1) return real(1);
     return j == 0 ? n.a : n.b;
 }
@@ -289,9 +306,9 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
                                              int s, typename Prec<MODE>::real* wrow, int gauss) {
     using real = typename Prec<MODE>::real;
     const int nr = a.nr;
-    const real* r = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
+    const real rc = (MODE == 0) ? (real)a.r_coef : (real)a.r_coeff;
     n.d = d;
-    if (d >= r[nr - 1]) {
+    if (d >= radius_at<real>(nr - 1, rc, a.r)) {
         n.kind = 1; n.lo = (int16_t)(nr - 1); n.npts = 1; n.a = real(1); n.b = real(1);
         return;
     }
@@ -305,7 +322,7 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
     int first = hi + 1, last = lo - 1;
     const bool keep = MODE == 0 && hi - lo + 1 <= MAXW;
     for (int i = lo; i <= hi; ++i) {
-        const real w = radial_w<real>(fabs(r[i] - d), hpar, gauss);
+        const real w = radial_w<real>(fabs(radius_at<real>(i, rc, a.r) - d), hpar, gauss);
         if (keep) wrow[i - lo] = w;
         if (w > real(0)) { S += w; first = min(first, i); last = i; }
     }
@@ -315,9 +332,9 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
         return;
     }
     int i = min(max((int)floor((real)a.eta * sqrt(real(2) * d)), 0), nr - 2);
-    while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
-    while (i > 0 && r[i] > d) --i;
-    const real ra = r[i], rb = r[i + 1];
+    while (i + 1 < nr - 1 && radius_at<real>(i + 1, rc, a.r) <= d) ++i;
+    while (i > 0 && radius_at<real>(i, rc, a.r) > d) --i;
+    const real ra = radius_at<real>(i, rc, a.r), rb = radius_at<real>(i + 1, rc, a.r);
     n.kind = 2; n.lo = (int16_t)i; n.npts = 2;
     n.a = (rb - d) / (rb - ra);
     n.b = (d - ra) / (rb - ra);
@@ -808,7 +825,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
     int nr = 0, nbins = 0, nq = 2, N = 0, L = 0;
     double *bins_a = nullptr, *bins_eps = nullptr, *bins_e = nullptr;
     uint32_t* stack = nullptr;
-    const real* rr = nullptr;
+    real rcoef = real(0);
     Scales sc{1.f, 1.f, 1.f};
 
     for (;;) {
@@ -836,7 +853,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             bins_eps = bins_a + nbins;
             bins_e = a.use_e ? bins_eps + nbins : nullptr;
             stack = reinterpret_cast<uint32_t*>(bins_a + (size_t)nq * nbins);
-            rr = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
+            rcoef = (MODE == 0) ? (real)a.r_coef : (real)a.r_coeff;
             if (MODE == 1) {                                     // fixed-point units from the root totals
                 real cm0[3], m0, q0[3], mi0;
                 load_node<MODE>(a.nodes, 0, cm0, m0, q0, mi0);
@@ -1028,7 +1045,7 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
                         const int b0 = (int)(en >> 16) * nr + n.lo;
                         const real wk = (real)(en & 0xffffu) * inv_m3;
                         for (int j = 0; j < n.npts; ++j) {
-                            const real w = spread_weight<MODE>(n, j, rr, s_w, VAR ? a.kern_a : 0) * wk;
+                            const real w = spread_weight<MODE>(n, j, rcoef, a.r, s_w, VAR ? a.kern_a : 0) * wk;
                             if (w == real(0)) continue;
                             if (n.alpha != real(0)) bin_atomic_add<MODE>(bins_a + b0 + j, w * n.alpha, sc.a);
                             if (a.use_e && n.e != real(0)) bin_atomic_add<MODE>(bins_e + b0 + j, w * n.e, sc.e);
@@ -1149,6 +1166,8 @@ WalkArgs make_args(const tr_tree* t) {
     a.th_if2 = t->p.theta_if * t->p.theta_if;
     a.th_src2 = t->p.theta_src * t->p.theta_src;
     a.lray = t->lray;
+    a.r_coef = 1.0 / (2.0 * (double)t->p.eta_r * (double)t->p.eta_r);
+    a.r_coeff = (float)a.r_coef;
     a.th_lim2f = (float)a.th_lim2; a.th_if2f = (float)a.th_if2; a.th_src2f = (float)a.th_src2;
     a.lrayf = (float)t->lray;
     a.toff = t->table->off; a.tent = t->table->ent; a.hdr = t->table->hdr;
