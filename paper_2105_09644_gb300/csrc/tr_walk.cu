@@ -992,7 +992,8 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             // block-wide offsets of the pushes and of the nodes to spread
             const unsigned om = __ballot_sync(FULL, action == 1);
             const unsigned bm = __ballot_sync(FULL, spread);
-            int pc = spread ? ne : 0;                             // (node, ray) pairs of this thread
+            // work items of this thread's node: (ray, point) triples (FP64) or rays (FP32)
+            int pc = spread ? (MODE == 0 ? ne * node.npts : ne) : 0;
             int incl = pc;
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(FULL, incl, o);
@@ -1026,29 +1027,73 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
             }
             __syncthreads();                                     // pushes and spread list visible
             if (overflow) break;
-            // spread the step's nodes: each thread takes a contiguous run of
-            // (node, table entry) pairs
-            if (ptotal > 0) {
-                const int chunk = (ptotal + NT - 1) / NT;
-                const int p0 = tid * chunk, p1 = min(p0 + chunk, ptotal);
-                if (p0 < p1) {
-                    int k = 0, hi = ntotal - 1;
-                    while (k < hi) {
-                        const int mid = (k + hi + 1) >> 1;
-                        if (s_pair0[mid] <= p0) k = mid; else hi = mid - 1;
-                    }
-                    RadialSpread<MODE> n = s_node[k];
-                    int kend = s_pair0[k + 1];
-                    for (int p = p0; p < p1; ++p) {
-                        if (p >= kend) { ++k; n = s_node[k]; kend = s_pair0[k + 1]; }
-                        const uint32_t en = __ldg(a.tent + n.off + (p - s_pair0[k]));
-                        const int b0 = (int)(en >> 16) * nr + n.lo;
-                        const real wk = (real)(en & 0xffffu) * inv_m3;
-                        for (int j = 0; j < n.npts; ++j) {
+            // spread the step's nodes.  FP64 form: each thread takes a contiguous
+            // run of (node, table entry, radial point) triples, so that every
+            // thread makes about the same number of deposits.  FP32 form: runs of
+            // (node, table entry) pairs with the points in an inner loop (the
+            // bookkeeping of the triples costs more than the balance gains there).
+            if constexpr (MODE == 0) {
+                if (ptotal > 0) {
+                    const int chunk = (ptotal + NT - 1) / NT;
+                    const int p0 = tid * chunk, p1 = min(p0 + chunk, ptotal);
+                    if (p0 < p1) {
+                        int k = 0, hi = ntotal - 1;
+                        while (k < hi) {
+                            const int mid = (k + hi + 1) >> 1;
+                            if (s_pair0[mid] <= p0) k = mid; else hi = mid - 1;
+                        }
+                        RadialSpread<MODE> n = s_node[k];
+                        const int li = p0 - s_pair0[k];
+                        int e = li / n.npts, j = li - e * n.npts;
+                        int ne_k = (s_pair0[k + 1] - s_pair0[k]) / n.npts;
+                        uint32_t en = __ldg(a.tent + n.off + e);
+                        int b0 = (int)(en >> 16) * nr + n.lo;
+                        real wk = (real)(en & 0xffffu) * inv_m3;
+                        for (int p = p0; p < p1; ++p) {
                             const real w = spread_weight<MODE>(n, j, rcoef, a.r, s_w, VAR ? a.kern_a : 0) * wk;
-                            if (w == real(0)) continue;
-                            if (n.alpha != real(0)) bin_atomic_add<MODE>(bins_a + b0 + j, w * n.alpha, sc.a);
-                            if (a.use_e && n.e != real(0)) bin_atomic_add<MODE>(bins_e + b0 + j, w * n.e, sc.e);
+                            if (w != real(0)) {
+                                if (n.alpha != real(0)) bin_atomic_add<MODE>(bins_a + b0 + j, w * n.alpha, sc.a);
+                                if (a.use_e && n.e != real(0)) bin_atomic_add<MODE>(bins_e + b0 + j, w * n.e, sc.e);
+                            }
+                            if (++j == n.npts) {                     // next table entry, or next node
+                                j = 0;
+                                if (++e == ne_k) {
+                                    if (p + 1 >= p1) break;
+                                    ++k;
+                                    n = s_node[k];
+                                    e = 0;
+                                    ne_k = (s_pair0[k + 1] - s_pair0[k]) / n.npts;
+                                }
+                                en = __ldg(a.tent + n.off + e);
+                                b0 = (int)(en >> 16) * nr + n.lo;
+                                wk = (real)(en & 0xffffu) * inv_m3;
+                            }
+                        }
+                    }
+                }
+            } else {
+                if (ptotal > 0) {
+                    const int chunk = (ptotal + NT - 1) / NT;
+                    const int p0 = tid * chunk, p1 = min(p0 + chunk, ptotal);
+                    if (p0 < p1) {
+                        int k = 0, hi = ntotal - 1;
+                        while (k < hi) {
+                            const int mid = (k + hi + 1) >> 1;
+                            if (s_pair0[mid] <= p0) k = mid; else hi = mid - 1;
+                        }
+                        RadialSpread<MODE> n = s_node[k];
+                        int kend = s_pair0[k + 1];
+                        for (int p = p0; p < p1; ++p) {
+                            if (p >= kend) { ++k; n = s_node[k]; kend = s_pair0[k + 1]; }
+                            const uint32_t en = __ldg(a.tent + n.off + (p - s_pair0[k]));
+                            const int b0 = (int)(en >> 16) * nr + n.lo;
+                            const real wk = (real)(en & 0xffffu) * inv_m3;
+                            for (int j = 0; j < n.npts; ++j) {
+                                const real w = spread_weight<MODE>(n, j, rcoef, a.r, s_w, VAR ? a.kern_a : 0) * wk;
+                                if (w == real(0)) continue;
+                                if (n.alpha != real(0)) bin_atomic_add<MODE>(bins_a + b0 + j, w * n.alpha, sc.a);
+                                if (a.use_e && n.e != real(0)) bin_atomic_add<MODE>(bins_e + b0 + j, w * n.e, sc.e);
+                            }
                         }
                     }
                 }
