@@ -316,8 +316,10 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
     const real hpar = gauss ? h : inv_h;
     const real reach = real(0.8661) * h;
     const real dlo = d > reach ? d - reach : real(0);
-    const int lo = max((int)floor((real)a.eta * sqrt(real(2) * dlo)) - 1, 0);
-    const int hi = min((int)ceil((real)a.eta * sqrt(real(2) * (d + reach))) + 1, nr - 1);
+    // floor / ceil of the support's index bounds (i = eta sqrt(2 r), Eq. 4):
+    // a rounding error below one index only widens the range by a point
+    const int lo = max((int)floor((real)a.eta * sqrt(real(2) * dlo)), 0);
+    const int hi = min((int)ceil((real)a.eta * sqrt(real(2) * (d + reach))), nr - 1);
     real S = real(0);
     int first = hi + 1, last = lo - 1;
     const bool keep = MODE == 0 && hi - lo + 1 <= MAXW;
