@@ -684,9 +684,9 @@ __device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* b
                     float zd = 1.f;                           // Eq. 17
                     if (bee) {
                         const float ev = bin_value_f<1>(bee + i + 1, ie) * __ldg(a.inv_volf + i + 1);
-                        if (ev > 0.f) zd = fminf(2.f, Fl / ev);
+                        if (ev > 0.f) zd = fminf(2.f, __fdividef(Fl, ev));
                     }
-                    cf = A * zd / Fl;                         // zeta_s = F_j / Ftot (Eq. 16)
+                    cf = __fdividef(A * zd, Fl);              // zeta_s = F_j / Ftot (Eq. 16)
                 } else {
                     go = false;
                 }
