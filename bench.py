@@ -357,15 +357,16 @@ def serving_run(args):
     from paper_2105_09644_gb300.serving import Server, poisson_stream, percentile
     sizes = tuple(int(x) for x in args.serving_sizes.split(","))
     nsides = tuple(int(x) for x in args.serving_nsides.split(","))
-    reqs = poisson_stream(args.serving, args.serving_rate, seed=2105, sizes=sizes, nsides=nsides, max_sources=1000)
-    srv = Server(budget_bytes=64 << 30, tick_targets=1 << 20, precision=1)
+    reqs = poisson_stream(args.serving, args.serving_rate, seed=2105, sizes=sizes, nsides=nsides, max_sources=1000,
+                          lazy=True)
+    srv = Server(budget_bytes=64 << 30, tick_targets=1 << 20, precision=1, keep_results=False)
     t0 = time.perf_counter()
     done = srv.run(reqs)
     wall = time.perf_counter() - t0
     lat = [1e3 * r.latency for r in done]
     rays = sum(r.N ** 3 * 12 * r.nside * r.nside for r in done)
     return {"requests": len(done), "arrival_rate_hz": args.serving_rate, "sizes": list(sizes),
-            "nsides": list(nsides), "sources": "1-1000 per request, log-uniform count",
+            "nsides": list(nsides), "sources": "1-1000 per request, log-uniform count", "theta_lim": 0.5,
             "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "max_ms": max(lat),
             "cell_rays_per_s": rays / wall, "wall_s": wall, "launches": srv.launches,
             "precision": "FP32 moments + FP64 sweep"}

@@ -39,6 +39,7 @@ class Request:
     nside: int = 2
     theta_lim: float = 0.5
     theta_src: float = math.inf
+    make: object = None                 # optional: fills n_H, src_xyz, src_Q when called (lazy request data)
     # filled by the server
     admitted: float | None = None
     done: float | None = None
@@ -130,9 +131,14 @@ class Scheduler:
 
 
 class Server:
-    """Scheduler plus the device work (tree builds and batched walks)."""
+    """Scheduler plus the device work (tree builds and batched walks).
 
-    def __init__(self, budget_bytes: int, tick_targets: int = 1 << 20, precision: int = 1, device=None):
+    keep_results=False returns each result to the host and keeps only a
+    summary (the flux total), for long streams whose results would not fit
+    in host memory together."""
+
+    def __init__(self, budget_bytes: int, tick_targets: int = 1 << 20, precision: int = 1, device=None,
+                 keep_results: bool = True):
         import torch
         from . import binding as B
         self.B = B
@@ -143,6 +149,7 @@ class Server:
         self.state: dict[int, dict] = {}
         self.t0 = time.perf_counter()
         self.launches = 0
+        self.keep_results = keep_results
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -163,10 +170,13 @@ class Server:
                                 precision=self.precision)
         d["tree"] = B.tr_build_tree(B.make_grid(d["n_H"], req.dx), B.make_sources(d["xyz"], d["Q"]), p)
         self.state[req.rid] = d
+        if req.make is not None:                 # the host copy of lazy request data is no longer needed
+            req.n_H = None
 
     def _finish(self, req: Request):
         d = self.state.pop(req.rid)
-        req.result = dict(F=d["F"].cpu().numpy(), e=d["e"].cpu().numpy(), ion=d["ion"].cpu().numpy())
+        res = dict(F=d["F"].cpu().numpy(), e=d["e"].cpu().numpy(), ion=d["ion"].cpu().numpy())
+        req.result = res if self.keep_results else dict(F_sum=float(res["F"].sum()), ionised=int(res["ion"].sum()))
 
     def tick(self) -> int:
         """Admit, launch one batch, retire; returns the number of targets done."""
@@ -183,39 +193,70 @@ class Server:
             self._finish(req)
         return sum(c for _, _, c in slices)
 
-    def run(self, requests: list[Request]) -> list[Request]:
-        """Replay requests at their arrival times (seconds after start)."""
+    def run(self, requests: list[Request], prefetch: int = 4) -> list[Request]:
+        """Replay requests at their arrival times (seconds after start).
+        Requests with lazy data are filled by a host thread in arrival order,
+        at most `prefetch` ahead of the ones already on the device."""
+        import threading
         pending = sorted(requests, key=lambda r: r.arrival)
+        ready = [threading.Event() for _ in pending]
+        slots = threading.Semaphore(prefetch)
+
+        def fill():
+            for k, r in enumerate(pending):
+                if r.make is not None:
+                    slots.acquire()
+                    r.make(r)
+                ready[k].set()
+
+        filler = threading.Thread(target=fill, daemon=True)
+        filler.start()
         self.t0 = time.perf_counter()
         i = 0
         while i < len(pending) or not self.sched.idle():
             now = self.now()
-            while i < len(pending) and pending[i].arrival <= now:
+            while i < len(pending) and pending[i].arrival <= now and ready[i].is_set():
                 self.submit(pending[i])
                 i += 1
+            started = [r for r in self.sched.waiting]
             if self.tick() == 0 and i < len(pending):
                 time.sleep(max(0.0, min(0.002, pending[i].arrival - self.now())))
+            for r in started:
+                if r.make is not None and r.admitted is not None and r.n_H is None:
+                    slots.release()
+        filler.join()
         return self.sched.finished
 
 
 def poisson_stream(n: int, rate_hz: float, seed: int, sizes=(32, 64, 128, 256), nsides=(2, 4),
-                   max_sources: int = 1000, box_pc: float = 10.0) -> list[Request]:
+                   max_sources: int = 1000, box_pc: float = 10.0, lazy: bool = False) -> list[Request]:
     """Seeded request stream: Poisson arrivals, grid size uniform over `sizes`,
-    log-normal k^-4 density, 1..max_sources sources (log-uniform count)."""
+    N_side uniform over `nsides`, theta_lim = 0.5, log-normal k^-4 density,
+    1..max_sources sources (log-uniform count).
+    lazy=True draws each request's density and sources only when the server
+    asks for them (the same values either way)."""
     from workloads import PC_CM, lognormal_density, uniform_sources
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
+    box = box_pc * PC_CM
+
+    def maker(k, N, S):
+        def make(req):
+            req.n_H = lognormal_density(N, seed * 1000 + k)
+            req.src_xyz, req.src_Q = uniform_sources(S, box, seed * 1000 + k + 500, 46.0, 49.0)
+        return make
+
     for k in range(n):
         t += rng.exponential(1.0 / rate_hz)
         N = int(rng.choice(sizes))
         nside = int(rng.choice(nsides))
         S = int(round(10 ** rng.uniform(0.0, math.log10(max_sources))))
-        box = box_pc * PC_CM
-        rho = lognormal_density(N, seed * 1000 + k)
-        xyz, q = uniform_sources(S, box, seed * 1000 + k + 500, 46.0, 49.0)
-        out.append(Request(k, t, N, box / N, rho, xyz, q, nside=nside,
-                           theta_lim=0.5 if nside == 2 else 0.25))
+        req = Request(k, t, N, box / N, None, None, None, nside=nside, theta_lim=0.5, make=maker(k, N, S))
+        if not lazy:
+            req.make(req)
+            req.make = None
+        out.append(req)
     return out
 
 

@@ -70,3 +70,41 @@ def test_oversized_request_is_refused():
 def test_percentile():
     xs = list(range(1, 101))
     assert percentile(xs, 50) == 50 and percentile(xs, 99) == 99 and percentile([], 50) is None
+
+
+def test_lazy_stream_is_filled_in_order_and_released():
+    """Requests with lazy data get their density when the server asks for
+    it, the same values as an eager stream, and the host copy is dropped
+    once the request is on the device (no GPU: the device work is stubbed)."""
+    from paper_2105_09644_gb300.serving import Server, poisson_stream
+
+    class HostOnly(Server):
+        def __init__(self, *a, **kw):
+            super().__init__(*a, **kw)
+            self.seen = []
+
+        def _start(self, req):
+            assert req.n_H is not None and req.n_H.shape == (req.N,) * 3
+            self.seen.append((req.rid, float(req.n_H.sum())))
+            if req.make is not None:
+                req.n_H = None
+
+        def tick(self):
+            for req in self.sched.admit(self.now()):
+                self._start(req)
+            slices = self.sched.plan()
+            if not slices:
+                return 0
+            for req in self.sched.complete(slices, self.now()):
+                req.result = {}
+            return sum(c for _, _, c in slices)
+
+    eager = poisson_stream(12, 500.0, seed=7, sizes=(8, 16), nsides=(2,), max_sources=10)
+    lazy = poisson_stream(12, 500.0, seed=7, sizes=(8, 16), nsides=(2,), max_sources=10, lazy=True)
+    assert all(r.n_H is None for r in lazy)
+    srv = HostOnly(budget_bytes=1 << 30, tick_targets=1 << 12, keep_results=False)
+    done = srv.run(lazy, prefetch=2)
+    assert len(done) == 12 and all(r.n_H is None for r in done)
+    sums = dict(srv.seen)
+    for r in eager:
+        assert sums[r.rid] == float(r.n_H.sum())
