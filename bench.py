@@ -319,9 +319,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {N}^3 log-normal (sigma_ln 1.5, k^-4), box 10 pc, "
-                               f"{len(w.src_Q)} point sources, N_PIX={w.npix}, N_R={r32['info']['nr']}, "
-                               f"theta_lim={w.theta_lim}",
+        "config": {"workload": workload_name(w, r32['info']['nr']),
                    "precision": "FP32 node moments (compensated), FP32 deposits summed exactly in 64-bit fixed point, FP64 photon budget in the sweep",
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"independent problem per GPU x{world}"},
@@ -374,6 +372,12 @@ def serving_run(args):
 
 # ---------------------------------------------------------------- reference arm
 
+def workload_name(w, nr):
+    """The workload as both arms name it in their config."""
+    return (f"{w.name}: {w.N}^3 log-normal (sigma_ln 1.5, k^-4), box 10 pc, {len(w.src_Q)} point sources, "
+            f"N_PIX={w.npix}, N_R={nr}, theta_lim={w.theta_lim}")
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step a bounded sample
     of the workload's targets."""
@@ -381,6 +385,9 @@ def run_reference(args):
     if rank != 0:
         return
     import multiprocessing as mp
+    import oracle
+    from workloads import workload
+    w = workload(args.workload)
     pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
     n = max(256, args.cpu_sample // 4)
     for _ in range(args.warmup):
@@ -396,7 +403,10 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": f"{args.workload} (oracle on a {n}-target sample per step)"},
+           "config": {"workload": workload_name(w, oracle.num_points(w.eta_r, w.N * math.sqrt(3.0))),
+                      "precision": "plain FP64 CPU oracle",
+                      "sample": f"{n} seeded random target cells per step",
+                      "parallelism": f"{r['cores']} host processes"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                             "sample": r["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
