@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-sample", type=int, default=100000,
+    ap.add_argument("--cpu-sample", type=int, default=300000,
                     help="targets in the CPU-oracle sample (about 10-15 s of oracle work on 16 cores)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=None)
