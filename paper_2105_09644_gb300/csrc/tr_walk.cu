@@ -799,8 +799,8 @@ __device__ __forceinline__ void deposit_cd(const WalkArgs& a, double* bins, uint
 }
 
 template <int MODE, int OUT, int NT, bool VAR>
-__global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
-                                            int n_jobs, unsigned int* counter) {
+__device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
+                                          int n_jobs, unsigned int* counter) {
     using real = typename Prec<MODE>::real;
     constexpr int NW = NT / 32, P = NT / 8;
     constexpr bool DUMP = OUT == OUT_DUMP, CD = OUT == OUT_CD;
@@ -1155,6 +1155,22 @@ __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, 
     if (cur >= 0) flush_counters(a, n_vis, n_acc, n_ent);
 }
 
+template <int MODE, int OUT, int NT, bool VAR>
+__global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
+                                            int n_jobs, unsigned int* counter) {
+    walk_body<MODE, OUT, NT, VAR>(jobs, job_end, n_jobs, counter);
+}
+
+// The same walk with registers capped so that six 128-thread CTAs fit an SM:
+// chosen when the ray bins are small enough for six (N_R <= ~30 at N_PIX 48)
+// and registers would otherwise hold the SM to five.
+template <int MODE, int OUT, int NT, bool VAR>
+__global__ void __launch_bounds__(NT, 6) k_walk_cap6(const WalkArgs* __restrict__ jobs,
+                                                     const int64_t* __restrict__ job_end, int n_jobs,
+                                                     unsigned int* counter) {
+    walk_body<MODE, OUT, NT, VAR>(jobs, job_end, n_jobs, counter);
+}
+
 // Unfused sweep over bins stored by the dump walk: one CTA per target.
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT) k_sweep_stored(WalkArgs a, const double* bins_in, const double* eps_self) {
@@ -1279,6 +1295,19 @@ bool wide_ctas(int mode, size_t smem) {
     return per_sm < 3;
 }
 
+// whether the register-capped walk fits more CTAs per SM than the plain one
+bool more_ctas_capped(const void* plain, const void* capped, size_t smem) {
+    int a = 0, b = 0;
+    if (cudaFuncSetAttribute(plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(capped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, plain, WALK_NT, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, capped, WALK_NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return b > a;
+}
+
 template <bool VAR>
 tr_status launch_jobs_v(int mode, int out, bool wide, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
                         int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
@@ -1298,6 +1327,8 @@ tr_status launch_jobs_v(int mode, int out, bool wide, size_t smem, const WalkArg
     if (mode == 0)
         return dump ? launch_persistent<T>(k_walk<0, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
                     : launch_persistent<T>(k_walk<0, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    if (!dump && more_ctas_capped((const void*)k_walk<1, F, T, VAR>, (const void*)k_walk_cap6<1, F, T, VAR>, smem))
+        return launch_persistent<T>(k_walk_cap6<1, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
     return dump ? launch_persistent<T>(k_walk<1, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
                 : launch_persistent<T>(k_walk<1, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
 }
