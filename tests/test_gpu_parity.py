@@ -298,3 +298,18 @@ def test_full_size_sourcecount256_sampled(B, orc, name):
     err = np.abs(F[targets][lit] - F_orc[lit]) / F_orc[lit]
     assert np.mean(err <= RTOL[1]) >= 0.97, (np.sort(err)[-5:])
     assert np.mean(ion[targets] == ion_orc) >= 0.97
+
+
+def test_bins_beyond_shared_memory_are_refused(B):
+    """Ray bins larger than a CTA's shared memory (here N_PIX 192 with
+    N_R 127 from a long L_ray) give TR_EUNSUPPORTED with a message, and the
+    library stays usable."""
+    import torch
+    w = small_turbulent(N=16)
+    n = dev(w.n_H)
+    with pytest.raises(B.TreeRayError) as ei:
+        B.solve(n, w.dx, nside=4, L_ray_cm=2000.0 * w.dx)
+    assert ei.value.status == B.TR_EUNSUPPORTED and "shared memory" in str(ei.value)
+    F, e, ion, it, dl = B.solve(n, w.dx)
+    torch.cuda.synchronize()
+    assert torch.isfinite(F).all()
