@@ -316,10 +316,12 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
     const real hpar = gauss ? h : inv_h;
     const real reach = real(0.8661) * h;
     const real dlo = d > reach ? d - reach : real(0);
-    // floor / ceil of the support's index bounds (i = eta sqrt(2 r), Eq. 4):
-    // a rounding error below one index only widens the range by a point
-    const int lo = max((int)floor((real)a.eta * sqrt(real(2) * dlo)), 0);
-    const int hi = min((int)ceil((real)a.eta * sqrt(real(2) * (d + reach))), nr - 1);
+    // floor / ceil of the support's index bounds (i = eta sqrt(2 r), Eq. 4),
+    // in FP32 in both forms: an error below one index only widens the range
+    // by a point, and the weights themselves are computed in the form's
+    // precision (an FP64 square root costs a dozen FP64-pipe instructions)
+    const int lo = max((int)floorf((float)a.eta * sqrtf(2.f * (float)dlo)), 0);
+    const int hi = min((int)ceilf((float)a.eta * sqrtf(2.f * (float)(d + reach))), nr - 1);
     real S = real(0);
     int first = hi + 1, last = lo - 1;
     const bool keep = MODE == 0 && hi - lo + 1 <= MAXW;
@@ -333,7 +335,7 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
         n.lo = (int16_t)first; n.npts = (int16_t)(last - first + 1); n.a = hpar; n.b = real(1) / S;
         return;
     }
-    int i = min(max((int)floor((real)a.eta * sqrt(real(2) * d)), 0), nr - 2);
+    int i = min(max((int)floorf((float)a.eta * sqrtf(2.f * (float)d)), 0), nr - 2);   // a guess, corrected below
     while (i + 1 < nr - 1 && radius_at<real>(i + 1, rc, a.r) <= d) ++i;
     while (i > 0 && radius_at<real>(i, rc, a.r) > d) --i;
     const real ra = radius_at<real>(i, rc, a.r), rb = radius_at<real>(i + 1, rc, a.r);
@@ -480,7 +482,7 @@ __device__ void deposit_eps(const WalkArgs& a, double* bins_eps, uint32_t off, i
     if (d >= r[nr - 1]) {
         i = nr - 2; w0 = real(0); w1 = real(1);
     } else {
-        i = min(max((int)floor((real)a.eta * sqrt(real(2) * d)), 0), nr - 2);
+        i = min(max((int)floorf((float)a.eta * sqrtf(2.f * (float)d)), 0), nr - 2);   // a guess, corrected below
         while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
         while (i > 0 && r[i] > d) --i;
         if (i == 0) {
