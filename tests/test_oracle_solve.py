@@ -124,3 +124,21 @@ def test_optically_thin_flux_kernels_agree(orc, kernel_eps):
     np.testing.assert_allclose(F, F_ref, rtol=1e-9)
     s = np.ravel_multi_index(src_cell[::-1], (N, N, N))
     assert F[s] == pytest.approx(1e48 / (4 * math.pi * (dx / 2) ** 2), rel=1e-9)
+
+
+def test_stromgren_iteration_converges_to_rs(orc):
+    """Outer iteration from a cold start (Sec. 2.6): a single source in a
+    uniform 16^3 medium converges (delta_cell < 1e-2) in fewer than 10
+    passes, with the ionised volume's equivalent radius at R_S (Eq. 17,
+    zeta_g off) within the radial resolution of the rays there."""
+    N, box = 16, 4.0 * PC_CM
+    dx = box / N
+    n, Q = 100.0, 3.3e47
+    w = Workload("s16", N, box, uniform_density(N, n), np.array([[8.5 * dx] * 3]), np.array([Q]), theta_src=1e-2)
+    F, e, ion, iters, delta = orc.solve(w, orc.params_for(w, zeta_g=False), max_iter=10, eps_lim=1e-2)
+    assert iters < 10 and delta < 1e-2
+    rs = (3 * Q / (4 * math.pi * n ** 2 * ALPHA_B)) ** (1 / 3) / dx
+    r_eff = (3 * ion.sum() / (4 * math.pi)) ** (1 / 3)
+    i = math.sqrt(2 * w.eta_r ** 2 * rs)
+    half_seg = 0.5 * (2 * i + 1) / (2 * w.eta_r ** 2)
+    assert abs(r_eff - rs) < max(1.0, half_seg), (r_eff, rs)
