@@ -1,21 +1,28 @@
-// Tree walk + node->ray mapping + far-to-near sweep, one warp per target.
+// Tree walk + node->ray mapping + far-to-near sweep, one CTA per target.
 //
-// Walk (Sec. 2.3-2.4): a warp keeps a stack of opened nodes in shared
-// memory.  Each step pops up to four opened nodes and evaluates their 32
-// children at once, one child per lane: a child that contains the target, or
-// fails the BH MAC (h/d < theta_lim), the IF MAC (nodes holding an
+// A persistent grid takes targets (cells) from a job list: a job is one
+// built tree and a range or list of its cells, so one launch can serve
+// several independent problems.
+// Walk (Sec. 2.3-2.4): the CTA keeps a stack of opened nodes in shared
+// memory.  Each step pops up to NT/8 opened nodes and evaluates their NT
+// children at once, one child per thread: a child that contains the target,
+// or fails the BH MAC (h/d < theta_lim), the IF MAC (nodes holding an
 // ionisation front: h/d < theta_IF) or the Src MAC (emitting nodes:
-// h/d < theta_src), is pushed as opened; the others are accepted.
-// Map (Sec. 2.3, App. A): every accepted node is spread by the warp over
-// the rays its table entry lists (angular weights) and over the evaluation
-// points its radial kernel reaches: W_p for the recombination rate alpha and
-// the energy e, W_f,3 for the emission eps.  The ray bins live in shared
-// memory; each node's (ray, point) cells are distinct, so the lanes write
-// without atomics, and in FP32 mode every bin is a compensated
-// (Kahan-Neumaier) pair.
-// Sweep (Sec. 2.5, Eq. 12-17): the bins become per-volume coefficients and
-// photon rates in FP64; each lane sweeps whole rays far to near and the warp
-// sums the rays (Eq. 18).
+// h/d < theta_src), is pushed as opened; the others are accepted.  On an
+// AMR tree a node flagged as a cell is never opened.
+// Map (Sec. 2.3, App. A): the nodes accepted in a step are spread by the
+// whole CTA over the rays their table entry lists (angular weights) and the
+// evaluation points their radial kernel reaches (W_p or W_g for the
+// recombination rate alpha and the energy e; W_f,3 or another flux kernel
+// for the emission eps), with shared-memory atomics into the ray bins: FP64
+// adds in the FP64 form, exact 64-bit fixed point in the FP32 form.
+// Sweep (Sec. 2.5, Eq. 12-17): each ray is swept far to near (FP64 form: a
+// thread per ray; FP32 form: two lanes per ray with FP64 only for the final
+// photon budget) and the CTA sums the rays (Eq. 18).
+// Variants: wide CTAs (512 / 256 threads) when the bins fill an SM, a
+// register-capped walk when six CTAs fit, a dump mode keeping the raw bins
+// and accepted ids, a column-density mode without radial points, and a
+// separate instantiation for non-default kernels and boundaries.
 #include <algorithm>
 #include <cstring>
 #include <vector>
