@@ -107,3 +107,34 @@ def test_monotone_in_alpha(orc):
         F0, _, _ = orc.sweep_ray(np.full(nr, alpha), eps, zeta_g=True)
         assert F0 <= prev
         prev = F0
+
+
+def test_zeta_s_shares_by_flux_at_the_segment_midpoint(orc):
+    """Two sources on a three-point ray, uniform alpha, zeta_d = zeta_g = 1.
+    Over [r_1, r_2] only the far source (j = 2) has photons to lose, so its
+    loss there is alpha dV_12 in full (zeta_s = 1, Eq. 14-15).  Over
+    [r_0, r_1] both sources share the segment's recombinations by zeta_s =
+    F_j / F (Eq. 16), the fluxes taken at the segment midpoint r_m = r_1 / 2
+    (reading R7): F_j = Phi_j / (r_j - r_m)^2.  Hence the ratio of their
+    losses there is R_02 / R_01 = (F_2 / F_1) (dV_02 / dV_01).  Sharing by
+    Phi_j instead would change the ratio by (r_2 - r_m)^2 / (r_1 - r_m)^2 = 49,
+    and fluxes taken at r_0 by (r_2 / r_1)^2 = 16, so either slip fails."""
+    eta = 2
+    r = [i * i / (2.0 * eta * eta) for i in range(3)]          # Eq. 4, in cells: 0, 1/8, 1/2
+    alpha = 0.5
+    eps = np.array([0.0, 30.0, 50.0])
+
+    def dV(i, j):                                              # Eq. 15
+        return ((r[j] - r[i]) ** 3 - (r[j] - r[i + 1]) ** 3) / 3.0
+
+    F0, phi0, loss = orc.sweep_ray(np.full(3, alpha), eps, eta_r=eta, zeta_g=False)
+    assert np.all(phi0[1:] > 0)                                # nothing clipped: every loss is R_ij
+    R12 = alpha * dV(1, 2)
+    R02 = loss[2] - R12
+    R01 = loss[1]
+    rm = 0.5 * (r[0] + r[1])
+    phi1, phi2 = eps[1] / FOUR_PI, eps[2] / FOUR_PI - R12
+    F1, F2 = phi1 / (r[1] - rm) ** 2, phi2 / (r[2] - rm) ** 2
+    assert R02 / R01 == pytest.approx((F2 / F1) * (dV(0, 2) / dV(0, 1)), rel=1e-10)
+    assert R01 == pytest.approx(alpha * dV(0, 1) * F1 / (F1 + F2), rel=1e-12)
+    assert (r[2] - rm) ** 2 / (r[1] - rm) ** 2 == pytest.approx(49.0)
