@@ -43,10 +43,26 @@ typedef enum {
     TR_EOVERFLOW = 6        /* a per-target walk stack overflowed; raise theta or report */
 } tr_status;
 
+/* Arithmetic of the three forms.  In both FP32 forms the node moments are
+ * FP32 with compensated (Kahan-Neumaier) sums over the children, the centre
+ * of mass stored as its offset from the node's geometric centre; the ray
+ * deposits are FP32 addends summed exactly in 64-bit fixed point (order
+ * independent, so the FP32 forms are bit-reproducible); and every opening
+ * decision (Sec. 2.4) and every discontinuous choice of the radial
+ * spreading that FP32 cannot settle within its certified error bound is
+ * re-taken in FP64 against an FP64 copy of the tree, so that the accepted
+ * node lists are those of the FP64 form, bit for bit.  The two FP32 forms
+ * differ only in the far-to-near sweep (Sec. 2.5, Eq. 12-17):
+ *  TR_FP32_SWEEP64: every segment's loss R_ij, the photon rates Phi_j and
+ *    their clipping at zero in FP64 (the FP32 coefficients widened), as in
+ *    the FP64 form;
+ *  TR_FP32_SWEEPDF: R_ij formed in FP32 and the budgets Phi_j carried as
+ *    unevaluated sums of two FP32 numbers (about 48 bits), with the final
+ *    Phi_j, the flux and the classification in FP64. */
 typedef enum {
     TR_FP64 = 0,            /* node moments, deposits and sweep all in FP64 */
-    TR_FP32_SWEEP64 = 1     /* FP32 node moments and ray deposits with compensated
-                               (Kahan-Neumaier) sums; FP64 sweep and classification */
+    TR_FP32_SWEEP64 = 1,    /* FP32 moments and deposits, FP64 sweep */
+    TR_FP32_SWEEPDF = 2     /* FP32 moments and deposits, double-FP32 sweep */
 } tr_precision;
 
 /* Radial kernels (App. A) that spread a node along a ray.  alpha and e use
@@ -246,24 +262,26 @@ tr_status tr_delta(const double* e_new, const double* e_old, int64_t n, int32_t 
 
 /* One pass of tr_solve (build + walk + map + sweep, max_iter = 1) that
  * allocates no device memory.  The paper has no counterpart: this is a
- * service to callers that cannot call cudaMalloc, such as code that runs
- * while a CUDA graph is being captured (an allocation would break or
- * escape the capture), applications whose device memory is owned by a pool
- * or arena that forbids outside allocations, and real-time or embedded hosts
- * that must not allocate once running.  The caller still supplies inputs and
- * outputs (as for tr_solve: N^3 device arrays, NULL allowed).
- * Working memory is one fixed device array (about 16 MB) inside the library,
- * held by every GPU that loads it until the process exits.  Limits: N <= 32,
- * N_side 1 or 2, N_R <= 128, max_iter = 1; larger requests return
- * TR_EUNSUPPORTED with a message and touch nothing.
- * The first call on a device looks up that array's device address and
- * builds the node->ray table into it, synchronising `stream`; make that
- * first call (and the first call with a new N_side) before any stream
- * capture.  All calls share the array and it keeps the last call's
- * contents; every value a pass needs is rewritten or cleared by that pass.
- * Calls whose GPU work overlaps (e.g. two streams driven from two host
- * threads that bypass its host lock) race on the array.  Synchronises
- * `stream`.  Errors: TR_EINVAL, TR_EUNSUPPORTED, TR_ECUDA, TR_EOVERFLOW. */
+ * service to callers that cannot call cudaMalloc, such as applications whose
+ * device memory is owned by a pool or arena that forbids allocations from
+ * outside it, and real-time or embedded hosts that must not allocate once
+ * running (cudaMalloc may block and synchronise the device).  The caller
+ * still supplies inputs and outputs (as for tr_solve: N^3 device arrays,
+ * NULL allowed) and gets the same results as tr_solve with the same
+ * parameters.  Working memory is one fixed device array (about 18 MB)
+ * inside the library, held by every GPU that loads it until the process
+ * exits.  Limits: N <= 32, N_side 1 or 2, N_R <= 128, max_iter = 1; larger
+ * requests return TR_EUNSUPPORTED with a message and touch nothing; other
+ * arguments are checked as tr_solve checks them.
+ * The first call on a device looks up that array's device address (with
+ * that device current) and builds the node->ray table into it; a call with
+ * a new N_side rebuilds the table.  Make the first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * every value a pass needs is rewritten or cleared by that pass.  Calls
+ * whose GPU work overlaps (e.g. two streams driven from two host threads
+ * that bypass its host lock) race on the array.  Every call synchronises
+ * `stream` before it returns.  Errors: TR_EINVAL, TR_EUNSUPPORTED, TR_ECUDA,
+ * TR_EOVERFLOW. */
 tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, const tr_params* p,
                            double* F_out, double* e_out, uint8_t* ion_out, tr_stream stream);
 
@@ -294,9 +312,11 @@ tr_status tr_tree_cells(const tr_tree* t, int64_t* n_cells);
  * (device array of n_nodes): 0 absent, 1 leaf (a cell), 2 parent. */
 tr_status tr_tree_flags(const tr_tree* t, uint8_t* out, tr_stream stream);
 
-/* Counters of the last walk over this tree (host output, 4 values):
- * nodes visited, nodes accepted, table entries read, deepest stack. */
-tr_status tr_tree_stats(const tr_tree* t, int64_t* out4);
+/* Counters of the last walk over this tree (host output, 6 values):
+ * nodes visited, nodes accepted, table entries read, deepest stack, and,
+ * in the FP32 forms, the opening decisions and the radial set-ups that were
+ * re-taken in FP64 because FP32 could not settle them (0 in the FP64 form). */
+tr_status tr_tree_stats(const tr_tree* t, int64_t* out6);
 
 /* Node records as FP64 in level-order Morton numbering, 8 values per node:
  * {m, cm_x, cm_y, cm_z, alpha_n, eps_n, e_n, m_ion}; m in n_H x cells,

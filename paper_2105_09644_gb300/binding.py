@@ -15,7 +15,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libtreeray.so")
 
 TR_OK, TR_EINVAL, TR_ENOMEM, TR_ECUDA, TR_ETIMEOUT, TR_EUNSUPPORTED, TR_EOVERFLOW = range(7)
-TR_FP64, TR_FP32_SWEEP64 = 0, 1
+TR_FP64, TR_FP32_SWEEP64, TR_FP32_SWEEPDF = 0, 1, 2
+PRECISIONS = (TR_FP64, TR_FP32_SWEEP64, TR_FP32_SWEEPDF)
 TR_KERNEL_WP, TR_KERNEL_WG = 0, 1
 TR_EPS_WF3, TR_EPS_WF1, TR_EPS_WF2, TR_EPS_WF3N, TR_EPS_WP, TR_EPS_WG = range(6)
 TR_BC_ISOLATED, TR_BC_PERIODIC, TR_BC_CORNER = 0, 1, 2
@@ -261,9 +262,10 @@ def tr_walk_sweep(tree: Tree, F=None, e=None, ion=None, stream=None):
 
 
 def tr_tree_stats(tree: Tree) -> dict:
-    out = (C.c_int64 * 4)()
+    out = (C.c_int64 * 6)()
     check(load().tr_tree_stats(tree.h, out))
-    return dict(visited=out[0], accepted=out[1], entries=out[2], max_stack=out[3])
+    return dict(visited=out[0], accepted=out[1], entries=out[2], max_stack=out[3], fp64_mac=out[4],
+                fp64_setup=out[5])
 
 
 def tr_solve(grid: Grid, sources: Sources, params: Params, F=None, e=None, ion=None, stream=None):

@@ -25,6 +25,8 @@ tr_status set_error(tr_status st, const char* fmt, ...) {
     return st;
 }
 
+void clear_error() { g_err[0] = '\0'; }
+
 tr_status cuda_check(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return TR_OK;
     if (e == cudaErrorMemoryAllocation) {
@@ -35,10 +37,9 @@ tr_status cuda_check(cudaError_t e, const char* what) {
 }
 
 namespace {
-
 constexpr double C_LIGHT = 2.99792458e10;   // cm s^-1
-
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+}  // namespace
 
 tr_status check_params(const tr_params* p) {
     if (!p) return set_error(TR_EINVAL, "params is NULL");
@@ -50,8 +51,8 @@ tr_status check_params(const tr_params* p) {
         return set_error(TR_EINVAL, "eta_r must be 1, 2, 4 or 8 (got %d)", p->eta_r);
     if (!(p->alpha_B > 0.0) || !std::isfinite(p->alpha_B)) return set_error(TR_EINVAL, "alpha_B must be finite and > 0");
     if (!(p->hnu > 0.0) || !std::isfinite(p->hnu)) return set_error(TR_EINVAL, "hnu must be finite and > 0");
-    if (p->precision != TR_FP64 && p->precision != TR_FP32_SWEEP64)
-        return set_error(TR_EINVAL, "precision must be TR_FP64 or TR_FP32_SWEEP64");
+    if (p->precision != TR_FP64 && p->precision != TR_FP32_SWEEP64 && p->precision != TR_FP32_SWEEPDF)
+        return set_error(TR_EINVAL, "precision must be TR_FP64, TR_FP32_SWEEP64 or TR_FP32_SWEEPDF");
     if (p->max_iter < 1) return set_error(TR_EINVAL, "max_iter must be >= 1");
     if (p->delta_mode != 0 && p->delta_mode != 1) return set_error(TR_EINVAL, "delta_mode must be 0 or 1");
     if (p->kernel_alpha != TR_KERNEL_WP && p->kernel_alpha != TR_KERNEL_WG)
@@ -82,6 +83,8 @@ tr_status check_grid(const tr_grid* g, const tr_sources* s) {
     return TR_OK;
 }
 
+namespace {
+
 template <typename T>
 tr_status dev_alloc(T** p, size_t bytes, const char* what) {
     if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
@@ -94,6 +97,9 @@ tr_status dev_alloc(T** p, size_t bytes, const char* what) {
 
 void tree_release(tr_tree* t) {
     if (!t) return;
+    if (t->nodes64 != t->nodes) cudaFree(t->nodes64);
+    if (t->sums64 != t->sums) cudaFree(t->sums64);
+    cudaFree(t->kappa);
     cudaFree(t->nodes);
     cudaFree(t->sums);
     cudaFree(t->ndot);
@@ -109,6 +115,20 @@ void tree_release(tr_tree* t) {
     cudaFree(t->blkmap);
     sweep_tables_free(&t->sw);
     delete t;
+}
+
+// The FP64 tree beside the FP32 record of the FP32 forms (mode 0: the tree
+// itself), and the device word of the centre-of-mass error bound.
+tr_status alloc_sidecar(tr_tree* t) {
+    if (t->mode == 0) {
+        t->nodes64 = t->nodes;
+        t->sums64 = t->sums;
+        return TR_OK;
+    }
+    tr_status rc = dev_alloc(&t->nodes64, sizeof(NodeF64) * (size_t)t->n_nodes, "FP64 tree nodes");
+    if (rc == TR_OK) rc = dev_alloc(&t->sums64, 3 * sizeof(double) * (size_t)t->n_nodes, "FP64 tree build sums");
+    if (rc == TR_OK) rc = dev_alloc(&t->kappa, sizeof(float), "centre-of-mass error bound");
+    return rc;
 }
 
 // Allocate (or reuse) a tree for this grid and parameters, then build it.
@@ -145,9 +165,10 @@ tr_status build(const tr_grid* g, const tr_sources* s, const tr_params* p, tr_tr
         t->nodes_bytes = (size_t)n_nodes * rec;
         if ((rc = dev_alloc(&t->nodes, t->nodes_bytes, "tree nodes")) != TR_OK ||
             (rc = dev_alloc(&t->sums, sum_bytes, "tree build sums")) != TR_OK ||
+            (rc = alloc_sidecar(t)) != TR_OK ||
             (rc = dev_alloc(&t->ndot, sizeof(double) * (size_t)N * N * N, "cell emission")) != TR_OK ||
             (rc = dev_alloc(&t->status, 4 * sizeof(int32_t), "status words")) != TR_OK ||
-            (rc = dev_alloc(&t->stats, 4 * sizeof(unsigned long long), "walk counters")) != TR_OK ||
+            (rc = dev_alloc(&t->stats, N_STATS * sizeof(unsigned long long), "walk counters")) != TR_OK ||
             (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK ||
             (rc = dev_alloc((unsigned char**)&t->jobbuf, walk_job_bytes(1), "walk job record")) != TR_OK) {
             tree_release(t);
@@ -263,9 +284,10 @@ tr_status build_amr(const tr_amr_grid* g, const tr_sources* s, const tr_params* 
     const size_t sum_bytes = (size_t)t->n_nodes * 3 * (mode == 0 ? sizeof(double) : sizeof(float));
     if ((rc = dev_alloc(&t->nodes, t->nodes_bytes, "tree nodes")) != TR_OK ||
         (rc = dev_alloc(&t->sums, sum_bytes, "tree build sums")) != TR_OK ||
+        (rc = alloc_sidecar(t)) != TR_OK ||
         (rc = dev_alloc(&t->ndot, sizeof(double) * (size_t)t->n_cells, "cell emission")) != TR_OK ||
         (rc = dev_alloc(&t->status, 4 * sizeof(int32_t), "status words")) != TR_OK ||
-        (rc = dev_alloc(&t->stats, 4 * sizeof(unsigned long long), "walk counters")) != TR_OK ||
+        (rc = dev_alloc(&t->stats, N_STATS * sizeof(unsigned long long), "walk counters")) != TR_OK ||
         (rc = dev_alloc(&t->counter, sizeof(unsigned int), "work counter")) != TR_OK ||
         (rc = dev_alloc((unsigned char**)&t->jobbuf, walk_job_bytes(1), "walk job record")) != TR_OK ||
         (rc = dev_alloc(&t->flags, (size_t)t->n_nodes, "node flags")) != TR_OK ||
@@ -505,15 +527,16 @@ tr_status tr_column_density(const tr_tree* t, const int64_t* targets, int64_t n_
     return rc;
 }
 
-tr_status tr_tree_stats(const tr_tree* t, int64_t* out4) {
+tr_status tr_tree_stats(const tr_tree* t, int64_t* out6) {
     g_err[0] = '\0';
-    if (!t || !out4) return set_error(TR_EINVAL, "tree or output is NULL");
-    unsigned long long h[4] = {0, 0, 0, 0};
+    if (!t || !out6) return set_error(TR_EINVAL, "tree or output is NULL");
+    unsigned long long h[N_STATS] = {};
     int32_t st[4] = {0, 0, 0, 0};
     tr_status rc = cuda_check(cudaMemcpy(h, t->stats, sizeof h, cudaMemcpyDeviceToHost), "stats copy");
     if (rc == TR_OK) rc = cuda_check(cudaMemcpy(st, t->status, sizeof st, cudaMemcpyDeviceToHost), "status copy");
     if (rc != TR_OK) return rc;
-    out4[0] = (int64_t)h[0]; out4[1] = (int64_t)h[1]; out4[2] = (int64_t)h[2]; out4[3] = st[1];
+    out6[0] = (int64_t)h[0]; out6[1] = (int64_t)h[1]; out6[2] = (int64_t)h[2]; out6[3] = st[1];
+    out6[4] = (int64_t)h[3]; out6[5] = (int64_t)h[4];
     return TR_OK;
 }
 

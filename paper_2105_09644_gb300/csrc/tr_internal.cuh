@@ -27,13 +27,18 @@ constexpr int MAX_LEVELS = 10;              // N <= 512
 constexpr int MAX_NR = 128;
 constexpr double PI_D = 3.14159265358979323846;
 constexpr double DELTA_IF = 1e-8;           // Sec. 2.4
+constexpr int N_STATS = 8;                  // walk counters per tree (see tr_tree::stats)
 
 // node topology of an AMR tree (one byte per node; uniform trees need none:
 // a node is a leaf exactly when it is on the finest level)
 constexpr uint8_t NODE_ABSENT = 0, NODE_LEAF = 1, NODE_PARENT = 2;
 
 struct NodeF64 { double cmx, cmy, cmz, m, alpha, eps, e, mion; };   // 64 B
-struct NodeF32 { float cmx, cmy, cmz, m, alpha, eps, e, mion; };    // 32 B
+// FP32 record: the centre of mass is kept as its offset (ox, oy, oz) from the
+// node's geometric centre, so that its rounding error scales with the node,
+// not with the box; the sign bit of mion marks a node that holds an
+// ionisation front (decided in FP64 when the tree is built).
+struct NodeF32 { float ox, oy, oz, m, alpha, eps, e, mion; };       // 32 B
 
 struct Table {                              // CSR: entries of key k are ent[off[k] .. off[k+1])
     int nside = 0;
@@ -92,11 +97,19 @@ struct tr_tree {
     double box_lo[3] = {0, 0, 0}, dx = 0, U = 0, Eu = 0, lray = 0;
     tr_params p{};
     int64_t n_nodes = 0;
-    void* nodes = nullptr;                  // NodeF64[n_nodes] or NodeF32[n_nodes]
-    void* sums = nullptr;                   // build scratch: FP64 {smx,smy,smz} or FP32 pairs
+    void* nodes = nullptr;                  // NodeF64[n_nodes] (mode 0) or NodeF32[n_nodes]
+    void* sums = nullptr;                   // build scratch: FP64 {smx,smy,smz} or FP32 offsets x mass
+    // FP32 forms: the same tree in FP64 (the walk re-decides in FP64 the few
+    // comparisons that FP32 cannot settle) and the bound kappa on the FP32
+    // centre-of-mass error, |cm32 - cm64| <= kappa x node edge; mode 0:
+    // nodes64 = nodes and kappa unused
+    void* nodes64 = nullptr;
+    void* sums64 = nullptr;
+    float* kappa = nullptr;
     double* ndot = nullptr;                 // N^3 mapped emission (photons s^-1)
     int32_t* status = nullptr;              // device status words: [0] overflowed targets, [1] deepest stack
-    unsigned long long* stats = nullptr;    // device counters of the last walk: visited, accepted, entries
+    unsigned long long* stats = nullptr;    // device counters of the last walk: visited, accepted, entries,
+                                            // MAC decisions and deposit set-ups redone in FP64
     unsigned int* counter = nullptr;        // persistent-kernel work counter
     const tr::Table* table = nullptr;
     tr::SweepTables sw;
@@ -129,9 +142,13 @@ struct tr_rays {
 
 namespace tr {
 
-// error reporting (tr_api.cu)
+// error reporting and argument checks (tr_api.cu)
 tr_status set_error(tr_status st, const char* fmt, ...);
+void clear_error();
 tr_status cuda_check(cudaError_t e, const char* what);
+tr_status check_params(const tr_params* p);
+tr_status check_grid(const tr_grid* g, const tr_sources* s);
+double default_lray(int N, const tr_params* p);   // cells
 
 // table (tr_table.cu)
 tr_status table_get(int nside, const Table** out, cudaStream_t st);
@@ -149,6 +166,8 @@ tr_status tree_build_amr(tr_tree* t, const double* n_H, const double* ndot, cons
 // AMR: flags and block map from t->blk (once per block layout)
 tr_status amr_topology(tr_tree* t, cudaStream_t st);
 tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st);
+// FP32 forms: IF flags and the centre-of-mass error bound from the FP64 tree
+tr_status finalize_f32(tr_tree* t, cudaStream_t st);
 tr_status flags_export(const tr_tree* t, uint8_t* out, cudaStream_t st);
 tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npix, int zeta_g,
                             cudaStream_t st);

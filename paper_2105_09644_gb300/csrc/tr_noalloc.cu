@@ -1,8 +1,9 @@
 // tr_solve_noalloc: one build + walk + sweep pass that allocates no device
-// memory.  Its working memory (mapped emission, tree nodes and build sums,
-// status words, ray tables and the node->ray table) lives in one file-scope
-// device array of fixed size, held by every GPU that loads the library until
-// the process exits.  See include/treeray.h for who needs it and its limits.
+// memory.  Its working memory (mapped emission, the FP64 tree and, for the
+// FP32 forms, the FP32 tree beside it, build sums, status words, ray tables
+// and the node->ray table) lives in one file-scope device array of fixed
+// size, held by every GPU that loads the library until the process exits.
+// See include/treeray.h for who needs it and its limits.
 #include <cmath>
 #include <mutex>
 
@@ -20,11 +21,14 @@ constexpr size_t NR2 = (size_t)MAX_NR * MAX_NR;
 
 constexpr size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t OFF_NDOT = 0;
-constexpr size_t OFF_NODES = up(OFF_NDOT + sizeof(double) * NA_NCELL);
+constexpr size_t OFF_NODES = up(OFF_NDOT + sizeof(double) * NA_NCELL);          // FP64 tree
 constexpr size_t OFF_SUMS = up(OFF_NODES + sizeof(NodeF64) * NA_NNODES);
-constexpr size_t OFF_STATUS = up(OFF_SUMS + 3 * sizeof(double) * NA_NNODES);
+constexpr size_t OFF_NODES32 = up(OFF_SUMS + 3 * sizeof(double) * NA_NNODES);   // FP32 tree (FP32 forms)
+constexpr size_t OFF_SUMS32 = up(OFF_NODES32 + sizeof(NodeF32) * NA_NNODES);
+constexpr size_t OFF_KAPPA = up(OFF_SUMS32 + 3 * sizeof(float) * NA_NNODES);
+constexpr size_t OFF_STATUS = up(OFF_KAPPA + sizeof(float));
 constexpr size_t OFF_STATS = up(OFF_STATUS + 4 * sizeof(int32_t));
-constexpr size_t OFF_COUNTER = up(OFF_STATS + 4 * sizeof(unsigned long long));
+constexpr size_t OFF_COUNTER = up(OFF_STATS + N_STATS * sizeof(unsigned long long));
 constexpr size_t OFF_JOB = up(OFF_COUNTER + sizeof(unsigned int));
 constexpr size_t JOB_BYTES = 1024;                // one walk job record (checked at run time)
 constexpr size_t OFF_R = up(OFF_JOB + JOB_BYTES);
@@ -42,12 +46,13 @@ constexpr size_t OFF_TCOUNTS = up(OFF_GIF + sizeof(float) * NR2);
 constexpr size_t OFF_TOFF = up(OFF_TCOUNTS + sizeof(uint32_t) * NKEYS);
 constexpr size_t OFF_THDR = up(OFF_TOFF + sizeof(uint32_t) * (NKEYS + 1));
 constexpr size_t OFF_TENT = up(OFF_THDR + sizeof(uint2) * NKEYS);
-constexpr size_t NA_BYTES = up(OFF_TENT + sizeof(uint32_t) * NA_ENT_CAP);   // about 16 MB
+constexpr size_t NA_BYTES = up(OFF_TENT + sizeof(uint32_t) * NA_ENT_CAP);   // about 18 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 constexpr double C_LIGHT = 2.99792458e10;
 constexpr int NA_MAX_DEVICES = 64;
+static_assert(NA_BYTES < (24u << 20), "the fixed working memory stays modest");
 
 struct DeviceState {
     bool ready = false;                          // symbol address resolved on this device
@@ -71,37 +76,22 @@ using namespace tr;
 
 extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, const tr_params* p, double* F_out,
                                       double* e_out, uint8_t* ion_out, tr_stream stream) {
+    clear_error();
     cudaStream_t st = (cudaStream_t)stream;
-    if (!g || !p) return set_error(TR_EINVAL, "grid or params is NULL");
-    if (!g->n_H) return set_error(TR_EINVAL, "n_H is NULL");
-    if (g->N < 8 || (g->N & (g->N - 1)) != 0)
-        return set_error(TR_EINVAL, "N must be a power of two >= 8 (got %d)", g->N);
+    // the checks of tr_solve, then the limits of the fixed working memory
+    tr_status rc0 = check_params(p);
+    if (rc0 == TR_OK) rc0 = check_grid(g, s);
+    if (rc0 != TR_OK) return rc0;
     if (g->N > NA_MAX_N)
         return set_error(TR_EUNSUPPORTED, "tr_solve_noalloc holds grids up to %d^3 cells in its fixed scratch (got %d^3)",
                          NA_MAX_N, g->N);
-    if (p->nside != 1 && p->nside != NA_MAX_NSIDE)
+    if (p->nside > NA_MAX_NSIDE)
         return set_error(TR_EUNSUPPORTED, "tr_solve_noalloc supports N_side 1 or 2 (got %d)", p->nside);
     if (p->max_iter != 1) return set_error(TR_EUNSUPPORTED, "tr_solve_noalloc runs one pass (max_iter = 1)");
-    if (!(p->theta_lim > 0.0) || !(p->theta_if > 0.0) || !(p->theta_src > 0.0))
-        return set_error(TR_EINVAL, "opening angles must be > 0");
-    if (p->eta_r != 1 && p->eta_r != 2 && p->eta_r != 4 && p->eta_r != 8)
-        return set_error(TR_EINVAL, "eta_r must be 1, 2, 4 or 8 (got %d)", p->eta_r);
-    if (p->precision != TR_FP64 && p->precision != TR_FP32_SWEEP64)
-        return set_error(TR_EINVAL, "precision must be TR_FP64 or TR_FP32_SWEEP64");
-    if (p->kernel_alpha != TR_KERNEL_WP && p->kernel_alpha != TR_KERNEL_WG)
-        return set_error(TR_EINVAL, "kernel_alpha must be TR_KERNEL_WP or TR_KERNEL_WG");
-    if (p->kernel_eps < TR_EPS_WF3 || p->kernel_eps > TR_EPS_WG)
-        return set_error(TR_EINVAL, "kernel_eps must be one of tr_eps_kernel");
-    if (!(p->alpha_B > 0.0) || !(p->hnu > 0.0) || !(g->dx > 0.0) || !std::isfinite(g->dx))
-        return set_error(TR_EINVAL, "alpha_B, hnu and dx must be > 0");
-    if (s && s->n < 0) return set_error(TR_EINVAL, "negative source count");
-    if (s && s->n > 0 && (!s->xyz || !s->Q)) return set_error(TR_EINVAL, "source arrays are NULL");
     const int N = g->N;
     int L = 0;
     while ((1 << L) < N) ++L;
-    if (p->bc < TR_BC_ISOLATED || p->bc > TR_BC_CORNER) return set_error(TR_EINVAL, "bc must be one of tr_bc");
-    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx
-                                          : (p->bc == TR_BC_CORNER ? 2.0 : 1.0) * (double)N * std::sqrt(3.0);
+    const double lray = p->L_ray_cm > 0.0 ? p->L_ray_cm / g->dx : default_lray(N, p);
     const int nr = p->eta_r * (int)std::floor(std::sqrt(2.0 * lray)) + 1;     // Eq. 5
     if (nr > MAX_NR || nr < 3) return set_error(TR_EUNSUPPORTED, "N_R = %d outside [3, %d]", nr, MAX_NR);
 
@@ -154,8 +144,16 @@ extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, con
     t.N = N; t.L = L; t.mode = p->precision;
     t.n_nodes = level_offset(L + 1);
     t.n_cells = NA_NCELL < (int64_t)N * N * N ? NA_NCELL : (int64_t)N * N * N;
-    t.nodes = ds.base + OFF_NODES;
-    t.sums = ds.base + OFF_SUMS;
+    t.nodes64 = ds.base + OFF_NODES;
+    t.sums64 = ds.base + OFF_SUMS;
+    if (t.mode == 0) {
+        t.nodes = t.nodes64;
+        t.sums = t.sums64;
+    } else {
+        t.nodes = ds.base + OFF_NODES32;
+        t.sums = ds.base + OFF_SUMS32;
+        t.kappa = at<float>(ds.base, OFF_KAPPA);
+    }
     t.ndot = at<double>(ds.base, OFF_NDOT);
     t.status = at<int32_t>(ds.base, OFF_STATUS);
     t.stats = at<unsigned long long>(ds.base, OFF_STATS);

@@ -6,7 +6,13 @@
 // (c = x | y << 1 | z << 2), so the eight children of a node are contiguous.
 // Leaves are the cells (level L = log2 N).  Parents are reduced from their
 // children in child order c = 0..7: plain FP64 sums, or FP32
-// Kahan-Neumaier (compensated) sums.
+// Kahan-Neumaier (compensated) sums.  The FP32 record keeps the centre of
+// mass as its offset from the node's geometric centre (first moments are
+// summed about each parent's centre), and the FP32 forms build the FP64 tree
+// beside it: the walk settles in FP64 the rare comparisons that FP32 cannot
+// (a bound kappa on the FP32 centre-of-mass error, per unit of node edge, is
+// measured here against the FP64 tree), and the IF flag of each node is
+// decided on the FP64 masses.
 #include "tr_internal.cuh"
 
 namespace tr {
@@ -72,17 +78,17 @@ __global__ void k_leaves(void* nodes_v, void* sums_v, int N, int L, const double
         double* sm = (double*)sums_v + 3 * id;
         sm[0] = sx; sm[1] = sy; sm[2] = sz;
     } else {
-        NodeF32 nd;
+        NodeF32 nd;                                 // a cell's mass sits at its centre: offset 0
         const float nf = (float)n;
         nd.m = nf;
-        nd.cmx = (float)ix + 0.5f; nd.cmy = (float)iy + 0.5f; nd.cmz = (float)iz + 0.5f;
+        nd.ox = 0.f; nd.oy = 0.f; nd.oz = 0.f;
         nd.alpha = (float)fmax(rec - src, 0.0);
         nd.eps = (float)fmax(src - rec, 0.0);
         nd.e = (float)(ep * invEu);
         nd.mion = (ep > 0.0) ? nf : 0.f;
         ((NodeF32*)nodes_v)[id] = nd;
         float* sm = (float*)sums_v + 3 * id;
-        sm[0] = nf * nd.cmx; sm[1] = nf * nd.cmy; sm[2] = nf * nd.cmz;
+        sm[0] = 0.f; sm[1] = 0.f; sm[2] = 0.f;
     }
 }
 
@@ -174,17 +180,17 @@ __global__ void k_amr_leaves(void* nodes_v, void* sums_v, int N, const int4* blk
         double* sm = (double*)sums_v + 3 * id;
         sm[0] = sx; sm[1] = sy; sm[2] = sz;
     } else {
-        NodeF32 nd;
+        NodeF32 nd;                                 // offset 0 from the cell's centre
         const float mf = (float)(n * vol);
         nd.m = mf;
-        nd.cmx = (float)px; nd.cmy = (float)py; nd.cmz = (float)pz;
+        nd.ox = 0.f; nd.oy = 0.f; nd.oz = 0.f;
         nd.alpha = (float)fmax(rec - src, 0.0);
         nd.eps = (float)fmax(src - rec, 0.0);
         nd.e = (float)(ep * invEu * vol);
         nd.mion = (ep > 0.0) ? mf : 0.f;
         ((NodeF32*)nodes_v)[id] = nd;
         float* sm = (float*)sums_v + 3 * id;
-        sm[0] = mf * nd.cmx; sm[1] = mf * nd.cmy; sm[2] = mf * nd.cmz;
+        sm[0] = 0.f; sm[1] = 0.f; sm[2] = 0.f;
     }
 }
 
@@ -222,28 +228,67 @@ __global__ void k_parents(void* nodes_v, void* sums_v, int l, int N, const uint8
         double* ps = (double*)sums_v + 3 * id;
         ps[0] = sx; ps[1] = sy; ps[2] = sz;
     } else {
+        // first moments about this node's centre: each child's own, plus its
+        // mass times the offset of its centre, +-s/4 per axis (a power of
+        // two, so the product is exact)
         const NodeF32* c = (const NodeF32*)nodes_v + ch;
         const float* cs = (const float*)sums_v + 3 * ch;
+        const float q4 = 0.25f * (float)s;
         F32Sum m_, sx, sy, sz, al, ep, ee, mi;
         for (int k = 0; k < 8; ++k) {
             const NodeF32 q = c[k];
+            const float mq = q.m * q4;
             m_.add(q.m); al.add(q.alpha); ep.add(q.eps); ee.add(q.e); mi.add(q.mion);
-            sx.add(cs[3 * k + 0]); sy.add(cs[3 * k + 1]); sz.add(cs[3 * k + 2]);
+            sx.add(cs[3 * k + 0]); sx.add((k & 1) ? mq : -mq);
+            sy.add(cs[3 * k + 1]); sy.add((k & 2) ? mq : -mq);
+            sz.add(cs[3 * k + 2]); sz.add((k & 4) ? mq : -mq);
         }
         NodeF32 p;
         p.m = m_.value(); p.alpha = al.value(); p.eps = ep.value(); p.e = ee.value(); p.mion = mi.value();
         const float fx = sx.value(), fy = sy.value(), fz = sz.value();
-        if (p.m > 0.f) { p.cmx = fx / p.m; p.cmy = fy / p.m; p.cmz = fz / p.m; }
-        else { p.cmx = (float)(((double)ix + 0.5) * s); p.cmy = (float)(((double)iy + 0.5) * s);
-               p.cmz = (float)(((double)iz + 0.5) * s); }
+        if (p.m > 0.f) { p.ox = fx / p.m; p.oy = fy / p.m; p.oz = fz / p.m; }
+        else { p.ox = 0.f; p.oy = 0.f; p.oz = 0.f; }           // no mass: the geometric centre
         ((NodeF32*)nodes_v)[id] = p;
         float* ps = (float*)sums_v + 3 * id;
         ps[0] = fx; ps[1] = fy; ps[2] = fz;
     }
 }
 
+// Level of node `id` in the level-order numbering.
+__device__ __forceinline__ int node_level(int64_t id) {
+    int l = 0;
+    while (level_offset(l + 1) <= id) ++l;
+    return l;
+}
+
+// FP32 forms, after both builds: the IF flag of every node (Sec. 2.4,
+// delta_IF m < m_ion < (1 - delta_IF) m on the FP64 masses, as the FP64 walk
+// decides it) goes into the sign bit of the FP32 m_ion, and kappa =
+// max |cm32 - cm64| / edge over the nodes that exist (rounded up).
+__global__ void k_finalize(NodeF32* nodes, const NodeF64* nodes64, const uint8_t* flags, int64_t n, int N,
+                           float* kappa) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float kap = 0.f;
+    if (i < n && !(flags && flags[i] == NODE_ABSENT)) {
+        const NodeF64 q = nodes64[i];
+        NodeF32& f = nodes[i];
+        const int l = node_level(i);
+        const uint32_t m = (uint32_t)(i - level_offset(l));
+        const double s = (double)(N >> l);
+        const double gx = ((double)compact3(m) + 0.5) * s, gy = ((double)compact3(m >> 1) + 0.5) * s,
+                     gz = ((double)compact3(m >> 2) + 0.5) * s;
+        const double ex = fabs(gx + (double)f.ox - q.cmx), ey = fabs(gy + (double)f.oy - q.cmy),
+                     ez = fabs(gz + (double)f.oz - q.cmz);
+        kap = __double2float_ru(fmax(ex, fmax(ey, ez)) / s);
+        const bool is_if = (__dmul_rn(DELTA_IF, q.m) < q.mion) && (q.mion < __dmul_rn(1.0 - DELTA_IF, q.m));
+        f.mion = is_if ? -fabsf(f.mion) : fabsf(f.mion);
+    }
+    for (int o = 16; o > 0; o >>= 1) kap = fmaxf(kap, __shfl_xor_sync(0xffffffffu, kap, o));
+    if ((threadIdx.x & 31) == 0 && kap > 0.f) atomicMax(reinterpret_cast<unsigned int*>(kappa), __float_as_uint(kap));
+}
+
 template <int MODE>
-__global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, double Eu) {
+__global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, double Eu, int N, const uint8_t* flags) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v[8];
@@ -251,10 +296,17 @@ __global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, 
         NodeF64 q = ((const NodeF64*)nodes_v)[i];
         v[0] = q.m; v[1] = q.cmx; v[2] = q.cmy; v[3] = q.cmz;
         v[4] = q.alpha; v[5] = q.eps; v[6] = q.e; v[7] = q.mion;
-    } else {
+    } else {                                       // centre of mass = geometric centre + offset
         NodeF32 q = ((const NodeF32*)nodes_v)[i];
-        v[0] = q.m; v[1] = q.cmx; v[2] = q.cmy; v[3] = q.cmz;
-        v[4] = q.alpha; v[5] = q.eps; v[6] = q.e; v[7] = q.mion;
+        const bool absent = flags && flags[i] == NODE_ABSENT;
+        const int l = node_level(i);
+        const uint32_t m = (uint32_t)(i - level_offset(l));
+        const double s = (double)(N >> l);
+        v[0] = q.m;
+        v[1] = absent ? 0.0 : ((double)compact3(m) + 0.5) * s + (double)q.ox;
+        v[2] = absent ? 0.0 : ((double)compact3(m >> 1) + 0.5) * s + (double)q.oy;
+        v[3] = absent ? 0.0 : ((double)compact3(m >> 2) + 0.5) * s + (double)q.oz;
+        v[4] = q.alpha; v[5] = q.eps; v[6] = q.e; v[7] = fabsf(q.mion);
     }
     v[4] *= U; v[5] *= U; v[6] *= Eu;
     for (int k = 0; k < 8; ++k) out[8 * i + k] = v[k];
@@ -356,6 +408,14 @@ void sweep_tables_free(SweepTables* sw) {
     *sw = SweepTables();
 }
 
+tr_status finalize_f32(tr_tree* t, cudaStream_t st) {
+    tr_status rc = cuda_check(cudaMemsetAsync(t->kappa, 0, sizeof(float), st), "clear kappa");
+    if (rc != TR_OK) return rc;
+    k_finalize<<<grid_for(t->n_nodes, 256), 256, 0, st>>>((NodeF32*)t->nodes, (const NodeF64*)t->nodes64, t->flags,
+                                                          t->n_nodes, t->N, t->kappa);
+    return cuda_check(cudaGetLastError(), "FP32 tree finalize kernel");
+}
+
 tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStream_t st) {
     const int64_t ncell = (int64_t)t->N * t->N * t->N;
     const double invU = 1.0 / t->U, invEu = 1.0 / t->Eu;
@@ -363,16 +423,22 @@ tr_status tree_build(tr_tree* t, const tr_grid* g, const tr_sources* s, cudaStre
     if (s && s->n > 0)
         k_map_sources<<<grid_for(s->n, 128), 128, 0, st>>>(t->ndot, t->N, g->box_lo[0], g->box_lo[1],
                                                            g->box_lo[2], g->dx, s->xyz, s->Q, s->n);
-    if (t->mode == 0)
-        k_leaves<0><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->L, g->n_H, t->ndot,
-                                                         g->e_prev, invU, invEu);
-    else
-        k_leaves<1><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->L, g->n_H, t->ndot,
-                                                         g->e_prev, invU, invEu);
+    // the FP64 tree (the whole tree in mode 0, the sidecar of the FP32 forms)
+    k_leaves<0><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes64, t->sums64, t->N, t->L, g->n_H, t->ndot,
+                                                     g->e_prev, invU, invEu);
     for (int l = t->L - 1; l >= 0; --l) {
         const int64_t nl = int64_t(1) << (3 * l);
-        if (t->mode == 0) k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, nullptr);
-        else k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, nullptr);
+        k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes64, t->sums64, l, t->N, nullptr);
+    }
+    if (t->mode != 0) {
+        k_leaves<1><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->L, g->n_H, t->ndot,
+                                                         g->e_prev, invU, invEu);
+        for (int l = t->L - 1; l >= 0; --l) {
+            const int64_t nl = int64_t(1) << (3 * l);
+            k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, nullptr);
+        }
+        tr_status rc = finalize_f32(t, st);
+        if (rc != TR_OK) return rc;
     }
     return cuda_check(cudaGetLastError(), "tree build kernels");
 }
@@ -393,21 +459,28 @@ tr_status tree_build_amr(tr_tree* t, const double* n_H, const double* ndot, cons
     const double invU = 1.0 / t->U, invEu = 1.0 / t->Eu;
     // nodes inside a cell are never written by the build: keep them zero
     tr_status rc = cuda_check(cudaMemsetAsync(t->nodes, 0, t->nodes_bytes, st), "clear nodes");
+    if (rc == TR_OK && t->nodes64 != t->nodes)
+        rc = cuda_check(cudaMemsetAsync(t->nodes64, 0, sizeof(NodeF64) * (size_t)t->n_nodes, st), "clear FP64 nodes");
     if (rc != TR_OK) return rc;
     k_ndot_init<<<grid_for(ncell, 256), 256, 0, st>>>(t->ndot, ndot, ncell);
     if (s && s->n > 0)
         k_amr_map_sources<<<grid_for(s->n, 128), 128, 0, st>>>(t->ndot, t->flags, t->blkmap, t->N, t->L, t->box_lo[0],
                                                                t->box_lo[1], t->box_lo[2], t->dx, s->xyz, s->Q, s->n);
-    if (t->mode == 0)
-        k_amr_leaves<0><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->blk, t->n_blocks, n_H,
-                                                             t->ndot, e_prev, invU, invEu);
-    else
-        k_amr_leaves<1><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->blk, t->n_blocks, n_H,
-                                                             t->ndot, e_prev, invU, invEu);
+    k_amr_leaves<0><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes64, t->sums64, t->N, t->blk, t->n_blocks, n_H,
+                                                         t->ndot, e_prev, invU, invEu);
     for (int l = t->L - 1; l >= 0; --l) {
         const int64_t nl = int64_t(1) << (3 * l);
-        if (t->mode == 0) k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, t->flags);
-        else k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, t->flags);
+        k_parents<0><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes64, t->sums64, l, t->N, t->flags);
+    }
+    if (t->mode != 0) {
+        k_amr_leaves<1><<<grid_for(ncell, 256), 256, 0, st>>>(t->nodes, t->sums, t->N, t->blk, t->n_blocks, n_H,
+                                                             t->ndot, e_prev, invU, invEu);
+        for (int l = t->L - 1; l >= 0; --l) {
+            const int64_t nl = int64_t(1) << (3 * l);
+            k_parents<1><<<grid_for(nl, 128), 128, 0, st>>>(t->nodes, t->sums, l, t->N, t->flags);
+        }
+        tr_status rc2 = finalize_f32(t, st);
+        if (rc2 != TR_OK) return rc2;
     }
     return cuda_check(cudaGetLastError(), "AMR tree build kernels");
 }
@@ -420,8 +493,10 @@ tr_status flags_export(const tr_tree* t, uint8_t* out, cudaStream_t st) {
 }
 
 tr_status tree_export(const tr_tree* t, double* out8, cudaStream_t st) {
-    if (t->mode == 0) k_export<0><<<grid_for(t->n_nodes, 256), 256, 0, st>>>(t->nodes, t->n_nodes, out8, t->U, t->Eu);
-    else k_export<1><<<grid_for(t->n_nodes, 256), 256, 0, st>>>(t->nodes, t->n_nodes, out8, t->U, t->Eu);
+    if (t->mode == 0)
+        k_export<0><<<grid_for(t->n_nodes, 256), 256, 0, st>>>(t->nodes, t->n_nodes, out8, t->U, t->Eu, t->N, t->flags);
+    else
+        k_export<1><<<grid_for(t->n_nodes, 256), 256, 0, st>>>(t->nodes, t->n_nodes, out8, t->U, t->Eu, t->N, t->flags);
     return cuda_check(cudaGetLastError(), "node export kernel");
 }
 

@@ -10,15 +10,22 @@
 // ionisation front: h/d < theta_IF) or the Src MAC (emitting nodes:
 // h/d < theta_src), is pushed as opened; the others are accepted.  On an
 // AMR tree a node flagged as a cell is never opened.
+// In the FP32 forms the distances come from FP32 records, and every opening
+// decision and every discontinuous choice of the radial spreading (beyond
+// L_ray or not, beyond the last point or not, a kernel support that is empty
+// or holds one point) that FP32 cannot settle within a certified bound on
+// its distance error is re-taken in FP64 from an FP64 copy of the tree: the
+// accepted nodes are those of the FP64 form, bit for bit.
 // Map (Sec. 2.3, App. A): the nodes accepted in a step are spread by the
 // whole CTA over the rays their table entry lists (angular weights) and the
 // evaluation points their radial kernel reaches (W_p or W_g for the
 // recombination rate alpha and the energy e; W_f,3 or another flux kernel
 // for the emission eps), with shared-memory atomics into the ray bins: FP64
-// adds in the FP64 form, exact 64-bit fixed point in the FP32 form.
-// Sweep (Sec. 2.5, Eq. 12-17): each ray is swept far to near (FP64 form: a
-// thread per ray; FP32 form: two lanes per ray with FP64 only for the final
-// photon budget) and the CTA sums the rays (Eq. 18).
+// adds in the FP64 form, exact 64-bit fixed point in the FP32 forms.
+// Sweep (Sec. 2.5, Eq. 12-17): each ray is swept far to near (FP64 and
+// FP32 + FP64-sweep forms: a thread per ray, FP64 arithmetic; FP32 +
+// double-FP32-sweep form: two lanes per ray, FP32 losses, double-FP32
+// budgets) and the CTA sums the rays (Eq. 18).
 // Variants: wide CTAs (512 / 256 threads) when the bins fill an SM, a
 // register-capped walk when six CTAs fit, a dump mode keeping the raw bins
 // and accepted ids, a column-density mode without radial points, and a
@@ -34,12 +41,18 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// MODE 0: FP64 form; 1: FP32 walk + FP64 sweep; 2: FP32 walk + double-FP32 sweep
 template <int MODE> struct Prec;
 template <> struct Prec<0> { using real = double; using Node = NodeF64; };
 template <> struct Prec<1> { using real = float; using Node = NodeF32; };
+template <> struct Prec<2> { using real = float; using Node = NodeF32; };
+
+constexpr float U32 = 5.9604645e-8f;        // 2^-24, the unit roundoff of FP32
 
 struct WalkArgs {
     const void* nodes;
+    const NodeF64* nodes64;                 // FP32 forms: the FP64 tree (exact re-decisions)
+    const float* kappa;                     // FP32 forms: |cm32 - cm64| <= kappa x edge
     int N, L, nr, npix, eta, nside, use_e, stack_cap;
     double th_lim2, th_if2, th_src2, lray;
     double r_coef;                          // r_i = i^2 r_coef cells, r_coef = 1 / (2 eta^2) (Eq. 4)
@@ -252,21 +265,57 @@ __device__ __forceinline__ bool must_open(double h2, double d2, double m, double
     const bool acc_src = !(eps > 0.0) || (h2 < __dmul_rn(a.th_src2, d2));
     return !(acc_lim && acc_if && acc_src);
 }
-__device__ __forceinline__ bool must_open(float h2, float d2, float m, float mion, float eps, const WalkArgs& a) {
-    const bool acc_lim = h2 < a.th_lim2f * d2;
-    const bool is_if = (1e-8f * m < mion) && (mion < (1.0f - 1e-8f) * m);
-    const bool acc_if = !is_if || (h2 < a.th_if2f * d2);
-    const bool acc_src = !(eps > 0.f) || (h2 < a.th_src2f * d2);
+// The same decision taken in FP64 with the node's IF flag given (FP32 forms,
+// when FP32 cannot settle it).
+__device__ __forceinline__ bool must_open_exact(double h2, double d2, bool is_if, bool has_eps, const WalkArgs& a) {
+    const bool acc_lim = h2 < __dmul_rn(a.th_lim2, d2);
+    const bool acc_if = !is_if || (h2 < __dmul_rn(a.th_if2, d2));
+    const bool acc_src = !has_eps || (h2 < __dmul_rn(a.th_src2, d2));
     return !(acc_lim && acc_if && acc_src);
+}
+
+// Bound on |d2 - d2_64| for an FP32 squared distance d2 whose per-axis
+// displacement carries an error of at most E from the stored centre of mass
+// (plus the rounding of the displacement, the squares and the sums): with
+// e_a <= E + u d per axis, |sum dx^2 - sum dx64^2| <= 2 sqrt3 d e + 3 e^2,
+// plus 3.1 u d2 of rounding; a factor 2 of margin on top.
+__device__ __forceinline__ float d2_err_bound(float d2, float E) {
+    const float d = d2 * rsqrtf(d2) * 1.000001f;
+    const float e = E + 1.01f * U32 * d;
+    return 2.f * (3.4641017f * d * e + 3.f * e * e + 3.1f * U32 * d2);
+}
+
+// One criterion h2 < t2 d2_64 with d2_64 in [lo, hi]: 1 surely true, 0 surely
+// false, -1 undecided (lo and hi carry the roundings of t2 and the product).
+__device__ __forceinline__ int mac_tri(float h2, float t2, float lo, float hi) {
+    if (h2 < t2 * lo) return 1;
+    if (h2 >= t2 * hi) return 0;
+    return -1;
+}
+
+// Opening decision of the FP32 forms: 1 open, 0 accept, -1 undecided within
+// the error bound B of d2 (then taken by must_open_exact on FP64 data).
+__device__ __forceinline__ int mac_f32(float h2, float d2, float B, bool is_if, bool has_eps, const WalkArgs& a) {
+    const float lo = fmaxf(d2 - B, 0.f) * (1.f - 8.f * U32);
+    const float hi = (d2 + B) * (1.f + 8.f * U32);
+    int r = mac_tri(h2, a.th_lim2f, lo, hi);
+    if (r == 0) return 1;
+    bool und = r < 0;
+    if (is_if) { r = mac_tri(h2, a.th_if2f, lo, hi); if (r == 0) return 1; und |= r < 0; }
+    if (has_eps) { r = mac_tri(h2, a.th_src2f, lo, hi); if (r == 0) return 1; und |= r < 0; }
+    return und ? -1 : 0;
 }
 
 __device__ __forceinline__ double dist2(double tx, double ty, double tz, const double* cm) {
     const double dx = __dsub_rn(tx, cm[0]), dy = __dsub_rn(ty, cm[1]), dz = __dsub_rn(tz, cm[2]);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
-__device__ __forceinline__ float dist2(float tx, float ty, float tz, const float* cm) {
-    const float dx = tx - cm[0], dy = ty - cm[1], dz = tz - cm[2];
-    return dx * dx + dy * dy + dz * dz;
+// FP32 forms: the squared distance of node nid from the target centre (tx,
+// ty, tz) in FP64 from the FP64 tree, exactly as the FP64 form computes it.
+__device__ __forceinline__ double exact_d2(const WalkArgs& a, int64_t nid, float tx, float ty, float tz) {
+    const double2 c01 = __ldg(reinterpret_cast<const double2*>(a.nodes64 + nid));
+    const double cm[3] = {c01.x, c01.y, __ldg(&a.nodes64[nid].cmz)};
+    return dist2((double)tx, (double)ty, (double)tz, cm);
 }
 
 // Radial spread of one accepted node (App. A), prepared by the thread that
@@ -307,21 +356,33 @@ __device__ __forceinline__ typename Prec<MODE>::real spread_weight(const RadialS
 }
 
 // W_p normalisation of an accepted node: the support of the kernel on the
-// evaluation points and 1/S.
+// evaluation points and 1/S.  FP32 forms (dtol = bound on the error of d):
+// returns true when a discontinuous choice -- d beyond the last point or
+// not, or a support that is empty or holds only points within rounding of
+// its edge (the normalisation then jumps between one point and the linear
+// split) -- is not settled in FP32; radial_setup_exact then takes it in FP64.
 template <int MODE>
-__device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename Prec<MODE>::real d,
-                                             int s, typename Prec<MODE>::real* wrow, int gauss) {
+__device__ __forceinline__ bool radial_setup(const WalkArgs& a, RadialSpread<MODE>& n, typename Prec<MODE>::real d,
+                                             int s, typename Prec<MODE>::real* wrow, int gauss, float dtol) {
     using real = typename Prec<MODE>::real;
     const int nr = a.nr;
     const real rc = (MODE == 0) ? (real)a.r_coef : (real)a.r_coeff;
     n.d = d;
-    if (d >= radius_at<real>(nr - 1, rc, a.r)) {
+    const real rlast = radius_at<real>(nr - 1, rc, a.r);
+    if (d >= rlast) {
         n.kind = 1; n.lo = (int16_t)(nr - 1); n.npts = 1; n.a = real(1); n.b = real(1);
-        return;
+        return MODE != 0 && (float)d - dtol < (float)rlast;
     }
+    if (MODE != 0 && (float)d + dtol >= (float)rlast) return true;
     const real h = (real)s, inv_h = real(1) / h;
     const real hpar = gauss ? h : inv_h;
-    const real reach = real(0.8661) * h;
+    const real reach = real(0.8661) * h + (real)dtol;
+    // a point whose kernel argument lies within xtol of sqrt3/2 may fall on
+    // the other side of the support's edge in FP64
+    const float xtol = MODE != 0 ? 2.f * (dtol + U32 * (2.f * (float)d + (float)reach)) * (float)inv_h + 4.f * U32
+                                 : 0.f;
+    int n_sure = 0;
+    bool near_edge = false;
     const real dlo = d > reach ? d - reach : real(0);
     // floor / ceil of the support's index bounds (i = eta sqrt(2 r), Eq. 4),
     // in FP32 in both forms: an error below one index only widens the range
@@ -333,14 +394,21 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
     int first = hi + 1, last = lo - 1;
     const bool keep = MODE == 0 && hi - lo + 1 <= MAXW;
     for (int i = lo; i <= hi; ++i) {
-        const real w = radial_w<real>(fabs(radius_at<real>(i, rc, a.r) - d), hpar, gauss);
+        const real dist = fabs(radius_at<real>(i, rc, a.r) - d);
+        const real w = radial_w<real>(dist, hpar, gauss);
         if (keep) wrow[i - lo] = w;
         if (w > real(0)) { S += w; first = min(first, i); last = i; }
+        if (MODE != 0) {
+            const bool ne = fabsf((float)(dist * inv_h) - (float)S3H_D) <= xtol;
+            near_edge |= ne;
+            n_sure += (w > real(0) && !ne) ? 1 : 0;
+        }
     }
+    if (MODE != 0 && near_edge && n_sure == 0) return true;
     if (S > real(0)) {
         n.kind = keep ? 3 : 0; n.woff = (uint8_t)(first - lo);
         n.lo = (int16_t)first; n.npts = (int16_t)(last - first + 1); n.a = hpar; n.b = real(1) / S;
-        return;
+        return false;
     }
     int i = min(max((int)floorf((float)a.eta * sqrtf(2.f * (float)d)), 0), nr - 2);   // a guess, corrected below
     while (i + 1 < nr - 1 && radius_at<real>(i + 1, rc, a.r) <= d) ++i;
@@ -349,6 +417,7 @@ __device__ __forceinline__ void radial_setup(const WalkArgs& a, RadialSpread<MOD
     n.kind = 2; n.lo = (int16_t)i; n.npts = 2;
     n.a = (rb - d) / (rb - ra);
     n.b = (d - ra) / (rb - ra);
+    return false;
 }
 
 // The other eps kernels (App. A.3), in FP64 whatever the form: emitting
@@ -365,6 +434,46 @@ __device__ __forceinline__ int bracket_d(const double* r, int nr, int eta, doubl
     while (i + 1 < nr - 1 && r[i + 1] <= d) ++i;
     while (i > 0 && r[i] > d) --i;
     return i;
+}
+
+// FP32 forms: the radial set-up of an accepted node taken on its FP64
+// distance d, when radial_setup could not settle it.  Only the supports
+// that FP32 left open reach here (at most two points, both at the edge, or
+// none), so the weights are stored explicitly: one point (weight 1), two
+// consecutive points, or the linear split between the points bracketing d.
+template <int MODE>
+__device__ void radial_setup_exact(const WalkArgs& a, RadialSpread<MODE>& n, double d, int s, int gauss) {
+    const int nr = a.nr;
+    n.d = (float)d;
+    if (d >= __ldg(a.r + nr - 1)) {
+        n.kind = 1; n.lo = (int16_t)(nr - 1); n.npts = 1; n.a = 1.f; n.b = 1.f;
+        return;
+    }
+    const double h = (double)s, inv_h = 1.0 / h, hpar = gauss ? h : inv_h;
+    const double reach = 0.8661 * h;
+    const int lo = max((int)floor((double)a.eta * sqrt(2.0 * fmax(d - reach, 0.0))) - 1, 0);
+    const int hi = min((int)ceil((double)a.eta * sqrt(2.0 * (d + reach))) + 1, nr - 1);
+    int first = -1, cnt = 0;
+    double w0 = 0.0, w1 = 0.0, S = 0.0;
+    for (int i = lo; i <= hi; ++i) {
+        const double w = radial_w<double>(fabs(__ldg(a.r + i) - d), hpar, gauss);
+        if (w > 0.0) {
+            if (cnt == 0) { first = i; w0 = w; } else if (cnt == 1) { w1 = w; }
+            S += w;
+            ++cnt;
+        }
+    }
+    if (cnt == 1) { n.kind = 1; n.lo = (int16_t)first; n.npts = 1; n.a = 1.f; n.b = 1.f; return; }
+    if (cnt == 2) { n.kind = 2; n.lo = (int16_t)first; n.npts = 2; n.a = (float)(w0 / S); n.b = (float)(w1 / S); return; }
+    if (cnt > 2) {                          // not reached (FP32 saw no point well inside); FP32 weights
+        n.kind = 0; n.lo = (int16_t)first; n.npts = (int16_t)cnt; n.a = (float)hpar; n.b = (float)(1.0 / S);
+        return;
+    }
+    const int i = bracket_d(a.r, nr, a.eta, d);
+    const double ra = __ldg(a.r + i), rb = __ldg(a.r + i + 1);
+    n.kind = 2; n.lo = (int16_t)i; n.npts = 2;
+    n.a = (float)((rb - d) / (rb - ra));
+    n.b = (float)((d - ra) / (rb - ra));
 }
 
 // two-point W_f,3: the sum and the flux at r = 0 exact
@@ -471,16 +580,19 @@ __device__ __forceinline__ void deposit_eps_variant(const WalkArgs& a, double* b
 }
 
 // Deposit of an emitting node's eps (App. A.3).  Default W_f,3: two points
-// r_i <= d < r_{i+1} keeping the sum and the flux at the target exact.
+// r_i <= d < r_{i+1} keeping the sum and the flux at the target exact (a
+// continuous function of d).  The other kernels take their FP64 distance
+// dvar (in the FP32 forms, from the FP64 tree: their choices jump).
 // Emitting nodes are few (they contain a source), so the accepting thread
 // does it alone.
 template <int MODE, bool VAR>
 __device__ void deposit_eps(const WalkArgs& a, double* bins_eps, uint32_t off, int ne,
-                            typename Prec<MODE>::real d, typename Prec<MODE>::real eps, float scale, int s_edge) {
+                            typename Prec<MODE>::real d, typename Prec<MODE>::real eps, float scale, int s_edge,
+                            double dvar) {
     using real = typename Prec<MODE>::real;
     const int nr = a.nr;
     if (VAR && a.kern_e != TR_EPS_WF3) {
-        deposit_eps_variant<MODE>(a, bins_eps, off, ne, (double)d, eps, scale, s_edge);
+        deposit_eps_variant<MODE>(a, bins_eps, off, ne, dvar, eps, scale, s_edge);
         return;
     }
     const real* r = (MODE == 0) ? reinterpret_cast<const real*>(a.r) : reinterpret_cast<const real*>(a.rf);
@@ -525,8 +637,9 @@ __device__ __forceinline__ double recip_nr(double a) {
 }
 
 // Recombination coefficient per unit volume at point i of a ray.  In the
-// FP32 form the deposits are FP32, so the coefficient is formed in FP32 and
-// widened; the photon budget itself (Phi_j and its losses) is FP64.
+// FP32 + FP64-sweep form the deposits are FP32, so the coefficient is formed
+// in FP32 and widened; the photon budget (Phi_j, its losses and their
+// clipping) is FP64.
 template <int MODE>
 __device__ __forceinline__ double alpha_at(const WalkArgs& a, const double* ba, int i, float inv_scale) {
     if (MODE == 0) return ba[i] * __ldg(a.inv_vol + i);
@@ -731,16 +844,17 @@ __device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* b
     return F0;
 }
 
-// Sum over the rays of one target (Eq. 18): FP64 form one thread per ray,
-// FP32 form one group of SG lanes per ray.
+// Sum over the rays of one target (Eq. 18): FP64 sweep (FP64 form and FP32 +
+// FP64-sweep form) one thread per ray, double-FP32 sweep one group of SG
+// lanes per ray.
 template <int MODE, int NT>
 __device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, double* bins_eps, double* bins_e,
                                              const Scales& sc) {
     const int nr = a.nr, tid = threadIdx.x;
     double Fk = 0.0;
-    if (MODE == 0) {
+    if (MODE != 2) {
         for (int k = tid; k < a.npix; k += NT)
-            Fk += sweep_ray<0>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
+            Fk += sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
     } else {
         const int gl = tid % SG, lane = tid & 31;
         const unsigned gmask = ((1u << SG) - 1u) << (lane & ~(SG - 1));
@@ -768,19 +882,28 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // One CTA of NT threads per target (persistent over targets).  Each step
 // pops NT/8 opened nodes and evaluates their NT children, one per thread.
 // Per-thread walk counters go to the job's counters (one atomic per warp).
-__device__ __forceinline__ void flush_counters(const WalkArgs& a, unsigned long long& n_vis, unsigned long long& n_acc,
-                                               unsigned long long& n_ent) {
+struct WalkCounters {
+    unsigned long long vis = 0, acc = 0, ent = 0;
+    unsigned fb_mac = 0, fb_dep = 0;        // FP32 forms: decisions re-taken in FP64
+};
+
+__device__ __forceinline__ void flush_counters(const WalkArgs& a, WalkCounters& c) {
+    unsigned long long fm = c.fb_mac, fd = c.fb_dep;
     for (int o = 16; o > 0; o >>= 1) {
-        n_vis += __shfl_xor_sync(FULL, n_vis, o);
-        n_acc += __shfl_xor_sync(FULL, n_acc, o);
-        n_ent += __shfl_xor_sync(FULL, n_ent, o);
+        c.vis += __shfl_xor_sync(FULL, c.vis, o);
+        c.acc += __shfl_xor_sync(FULL, c.acc, o);
+        c.ent += __shfl_xor_sync(FULL, c.ent, o);
+        fm += __shfl_xor_sync(FULL, fm, o);
+        fd += __shfl_xor_sync(FULL, fd, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(a.stats + 0, n_vis);
-        atomicAdd(a.stats + 1, n_acc);
-        atomicAdd(a.stats + 2, n_ent);
+        atomicAdd(a.stats + 0, c.vis);
+        atomicAdd(a.stats + 1, c.acc);
+        atomicAdd(a.stats + 2, c.ent);
+        if (fm) atomicAdd(a.stats + 3, fm);
+        if (fd) atomicAdd(a.stats + 4, fd);
     }
-    n_vis = n_acc = n_ent = 0;
+    c = WalkCounters();
 }
 
 // One CTA of NT threads per target, persistent over the targets of a list of
@@ -831,7 +954,8 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
     const unsigned lanemask_lt = (1u << lane) - 1u;
     const real inv_m3 = real(1.0) / real(TM * TM * TM);
     const int64_t total = job_end[n_jobs - 1];
-    unsigned long long n_vis = 0, n_acc = 0, n_ent = 0;      // per-thread counters
+    WalkCounters cnt;                                        // per-thread counters
+    float kap = 0.f;                                         // FP32 forms: the tree's kappa
     int cur = -1;
     int nr = 0, nbins = 0, nq = 2, N = 0, L = 0;
     double *bins_a = nullptr, *bins_eps = nullptr, *bins_e = nullptr;
@@ -852,7 +976,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
         const int64_t qg = (int64_t)s_q;
         if (j < 0) break;
         if (j != cur) {                                          // load the job (uniform over the CTA)
-            if (cur >= 0) flush_counters(a, n_vis, n_acc, n_ent);
+            if (cur >= 0) flush_counters(a, cnt);
             __syncthreads();
             const int* src = reinterpret_cast<const int*>(jobs + j);
             int* dst = reinterpret_cast<int*>(&s_a);
@@ -865,12 +989,13 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
             bins_e = a.use_e ? bins_eps + nbins : nullptr;
             stack = reinterpret_cast<uint32_t*>(bins_a + (size_t)nq * nbins);
             rcoef = (MODE == 0) ? (real)a.r_coef : (real)a.r_coeff;
-            if (MODE == 1) {                                     // fixed-point units from the root totals
+            if (MODE != 0) {                                     // fixed-point units from the root totals
                 real cm0[3], m0, q0[3], mi0;
                 load_node<MODE>(a.nodes, 0, cm0, m0, q0, mi0);
                 sc.a = fixed_scale((float)q0[0]);
                 sc.eps = fixed_scale((float)q0[1]);
                 sc.e = fixed_scale((float)q0[2]);
+                kap = __ldg(a.kappa) * 1.000001f;
             }
         }
         const int64_t q = qg - (j > 0 ? job_end[j - 1] : 0);    // index within the job
@@ -941,7 +1066,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
             // ROOT_EVAL: the root itself is evaluated (a mirror image does not
             // contain the target, so its root is subject to the MACs)
             if (pi < np && (!VAR || pe != ROOT_EVAL || c == 0)) {
-                ++n_vis;
+                ++cnt.vis;
                 lev = (VAR && pe == ROOT_EVAL) ? 0 : (int)(pe >> 27) + 1;
                 mort = (VAR && pe == ROOT_EVAL) ? 0u : (((pe & 0x7ffffffu) << 3) | (uint32_t)c);
                 const int s = N >> lev;
@@ -966,30 +1091,79 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                         bc_frame<real>(a.bc, (img >> 1) & 1, N, 2 * cy + s, 2 * ty + ts, py, oy, qy);
                         bc_frame<real>(a.bc, (img >> 2) & 1, N, 2 * cz + s, 2 * tz + ts, pz, oz, qz);
                     }
-                    const real d2 = dist2(qx, qy, qz, cm);
+                    real d2;
+                    float B = 0.f;                       // FP32 forms: bound on |d2 - d2 in FP64|
+                    if constexpr (MODE == 0) {
+                        d2 = dist2(qx, qy, qz, cm);
+                    } else {
+                        // centre of mass - target = o/2 + offset (a mirror image
+                        // of the corner of symmetry mirrors the offset too)
+                        const bool mir = VAR && a.bc == TR_BC_CORNER;
+                        const float ex = fmaf(0.5f, (float)ox, (mir && (img & 1)) ? -cm[0] : cm[0]);
+                        const float ey = fmaf(0.5f, (float)oy, (mir && (img & 2)) ? -cm[1] : cm[1]);
+                        const float ez = fmaf(0.5f, (float)oz, (mir && (img & 4)) ? -cm[2] : cm[2]);
+                        d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        B = d2_err_bound(d2, kap * (float)s);
+                    }
                     const real h2 = (real)s * (real)s;
-                    if (!leaf && must_open(h2, d2, m, mion, qv[1], a)) {
+                    bool open = false;
+                    if (!leaf) {
+                        if constexpr (MODE == 0) {
+                            open = must_open(h2, d2, m, mion, qv[1], a);
+                        } else {
+                            const int r = mac_f32(h2, d2, B, signbit(mion), qv[1] > 0.f, a);
+                            if (r < 0) {
+                                ++cnt.fb_mac;
+                                open = must_open_exact((double)h2, exact_d2(a, nid, qx, qy, qz), signbit(mion),
+                                                       qv[1] > 0.f, a);
+                            } else {
+                                open = r == 1;
+                            }
+                        }
+                    }
+                    if (open) {
                         action = 1;
                     } else if (CD) {
                         action = 2;
                         if (m > real(0)) {
                             const uint2 hd = __ldg(a.hdr + table_key(ox, oy, oz, s));
-                            n_ent += hd.y;
+                            cnt.ent += hd.y;
                             deposit_cd<MODE>(a, bins_a, hd.x, (int)hd.y, m, sqrt(d2));
                         }
                     } else {
                         action = 2;
                         const real d = sqrt(d2);
-                        const bool in_reach = (MODE == 0) ? ((double)d <= a.lray) : ((float)d <= a.lrayf);
+                        // FP32 forms: |d - d64| <= dtol; the choices that jump
+                        // with d and lie closer than that are taken on d64
+                        const float dtol = MODE != 0 ? B / (float)d + 4.f * U32 * (float)d : 0.f;
+                        double d64 = -1.0;
+                        auto exact_d = [&]() -> double {
+                            if (d64 < 0.0) { d64 = sqrt(exact_d2(a, nid, qx, qy, qz)); ++cnt.fb_dep; }
+                            return d64;
+                        };
+                        bool in_reach;
+                        if constexpr (MODE == 0) {
+                            in_reach = d <= a.lray;
+                        } else {
+                            if ((float)d + dtol < a.lrayf * (1.f - 2.f * U32)) in_reach = true;
+                            else if ((float)d - dtol > a.lrayf * (1.f + 2.f * U32)) in_reach = false;
+                            else in_reach = exact_d() <= a.lray;
+                        }
                         const bool has_ae = qv[0] != real(0) || (a.use_e && qv[2] != real(0));
                         if (in_reach && (has_ae || qv[1] != real(0))) {
                             const int key = table_key(ox, oy, oz, s);
                             const uint2 hd = __ldg(a.hdr + key);
                             ne = (int)hd.y;
-                            n_ent += ne;
-                            if (qv[1] != real(0)) deposit_eps<MODE, VAR>(a, bins_eps, hd.x, ne, d, qv[1], sc.eps, s);
+                            cnt.ent += ne;
+                            if (qv[1] != real(0)) {
+                                const double dvar = (MODE != 0 && VAR && a.kern_e != TR_EPS_WF3) ? exact_d() : (double)d;
+                                deposit_eps<MODE, VAR>(a, bins_eps, hd.x, ne, d, qv[1], sc.eps, s, dvar);
+                            }
                             if (has_ae && ne > 0) {
-                                radial_setup<MODE>(a, node, d, s, s_w + tid * MAXW, VAR ? a.kern_a : 0);
+                                const int gauss = VAR ? a.kern_a : 0;
+                                if (radial_setup<MODE>(a, node, d, s, s_w + tid * MAXW, gauss, dtol)) {
+                                    if constexpr (MODE != 0) radial_setup_exact<MODE>(a, node, exact_d(), s, gauss);
+                                }
                                 node.src = (uint16_t)tid;
                                 node.alpha = qv[0];
                                 node.e = a.use_e ? qv[2] : real(0);
@@ -1030,7 +1204,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                 if (tid == 0) s_pair0[ntotal] = ptotal;
             }
             if (action == 2) {
-                ++n_acc;
+                ++cnt.acc;
                 if (DUMP) {
                     const int slot = atomicAdd(&s_nacc, 1);
                     if (slot < a.acc_cap) a.ids_out[q * a.acc_cap + slot] = (int32_t)(level_offset(lev) + mort);
@@ -1161,7 +1335,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
             if (a.ion) a.ion[o] = (uint8_t)(F > 0.0);
         }
     }
-    if (cur >= 0) flush_counters(a, n_vis, n_acc, n_ent);
+    if (cur >= 0) flush_counters(a, cnt);
 }
 
 template <int MODE, int OUT, int NT, bool VAR>
@@ -1231,6 +1405,8 @@ size_t walk_smem(const tr_tree* t) {
 WalkArgs make_args(const tr_tree* t) {
     WalkArgs a{};
     a.nodes = t->nodes;
+    a.nodes64 = (const NodeF64*)t->nodes64;
+    a.kappa = t->kappa;
     a.N = t->N; a.L = t->L; a.nr = t->nr; a.npix = t->npix; a.eta = t->p.eta_r; a.nside = t->p.nside;
     a.use_e = t->use_e;
     a.stack_cap = STACK_CAP;
@@ -1292,16 +1468,20 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const i
     return cuda_check(cudaGetLastError(), "walk kernel launch");
 }
 
-bool wide_ctas(int mode, size_t smem) {
+template <int MODE>
+bool wide_ctas_m(size_t smem) {
     int per_sm = 0;
-    const void* k = mode == 0 ? (const void*)k_walk<0, OUT_FUSED, WALK_NT, false>
-                              : (const void*)k_walk<1, OUT_FUSED, WALK_NT, false>;
+    const void* k = (const void*)k_walk<MODE, OUT_FUSED, WALK_NT, false>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WALK_NT, smem) != cudaSuccess) {
         cudaGetLastError();
         return true;                                             // too large for 128 threads: try wide
     }
     return per_sm < 3;
+}
+
+bool wide_ctas(int mode, size_t smem) {
+    return mode == 0 ? wide_ctas_m<0>(smem) : (mode == 1 ? wide_ctas_m<1>(smem) : wide_ctas_m<2>(smem));
 }
 
 // whether the register-capped walk fits more CTAs per SM than the plain one
@@ -1317,36 +1497,43 @@ bool more_ctas_capped(const void* plain, const void* capped, size_t smem) {
     return b > a;
 }
 
+// The walk kernel of one form and output.  MODE 2 (double-FP32 sweep) only
+// differs from MODE 1 in the sweep, so its dump and column-density walks are
+// those of MODE 1 (chosen by launch_jobs).
+template <int MODE, bool VAR>
+tr_status launch_mode(int out, bool wide, size_t smem, const WalkArgs* jobs, const int64_t* job_end, int n_jobs,
+                      int64_t total, unsigned int* counter, cudaStream_t st) {
+    constexpr int W = MODE == 0 ? WALK_NT_WIDE_F64 : WALK_NT_WIDE_F32, T = WALK_NT;
+    constexpr int F = OUT_FUSED;
+    if constexpr (MODE != 2) {
+        constexpr int D = OUT_DUMP, C = OUT_CD;
+        if (out == C) return launch_persistent<T>(k_walk<MODE, C, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+        if (out == D)
+            return wide ? launch_persistent<W>(k_walk<MODE, D, W, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
+                        : launch_persistent<T>(k_walk<MODE, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    }
+    if (wide) return launch_persistent<W>(k_walk<MODE, F, W, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    if constexpr (MODE != 0) {
+        if (more_ctas_capped((const void*)k_walk<MODE, F, T, VAR>, (const void*)k_walk_cap6<MODE, F, T, VAR>, smem))
+            return launch_persistent<T>(k_walk_cap6<MODE, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    }
+    return launch_persistent<T>(k_walk<MODE, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+}
+
 template <bool VAR>
 tr_status launch_jobs_v(int mode, int out, bool wide, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
                         int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
-    constexpr int W0 = WALK_NT_WIDE_F64, W1 = WALK_NT_WIDE_F32, T = WALK_NT;
-    constexpr int F = OUT_FUSED, D = OUT_DUMP, C = OUT_CD;
-    if (out == C)                                                // N_PIX bins only: never wide
-        return mode == 0 ? launch_persistent<T>(k_walk<0, C, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                         : launch_persistent<T>(k_walk<1, C, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-    const bool dump = out == D;
-    if (wide) {
-        if (mode == 0)
-            return dump ? launch_persistent<W0>(k_walk<0, D, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                        : launch_persistent<W0>(k_walk<0, F, W0, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-        return dump ? launch_persistent<W1>(k_walk<1, D, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent<W1>(k_walk<1, F, W1, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-    }
-    if (mode == 0)
-        return dump ? launch_persistent<T>(k_walk<0, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                    : launch_persistent<T>(k_walk<0, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-    if (!dump && more_ctas_capped((const void*)k_walk<1, F, T, VAR>, (const void*)k_walk_cap6<1, F, T, VAR>, smem))
-        return launch_persistent<T>(k_walk_cap6<1, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
-    return dump ? launch_persistent<T>(k_walk<1, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                : launch_persistent<T>(k_walk<1, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    if (mode == 0) return launch_mode<0, VAR>(out, wide, smem, jobs, job_end, n_jobs, total, counter, st);
+    if (mode == 1 || out != OUT_FUSED)
+        return launch_mode<1, VAR>(out, wide, smem, jobs, job_end, n_jobs, total, counter, st);
+    return launch_mode<2, VAR>(out, wide, smem, jobs, job_end, n_jobs, total, counter, st);
 }
 
 // var: some job uses a kernel choice other than W_p / W_f,3 or a boundary
 // other than isolated
 tr_status launch_jobs(int mode, int out, bool var, size_t smem, const WalkArgs* jobs, const int64_t* job_end,
                       int n_jobs, int64_t total, unsigned int* counter, cudaStream_t st) {
-    const bool wide = out != OUT_CD && wide_ctas(mode, smem);
+    const bool wide = out != OUT_CD && wide_ctas(out == OUT_FUSED ? mode : (mode != 0 ? 1 : 0), smem);
     return var ? launch_jobs_v<true>(mode, out, wide, smem, jobs, job_end, n_jobs, total, counter, st)
                : launch_jobs_v<false>(mode, out, wide, smem, jobs, job_end, n_jobs, total, counter, st);
 }
@@ -1375,7 +1562,7 @@ tr_status walk_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, 
     memcpy(host, &a, sizeof(WalkArgs));
     memcpy(host + sizeof(WalkArgs), &n_targets, sizeof(int64_t));
     tr_status s = cuda_check(cudaMemsetAsync(t->status, 0, 4 * sizeof(int32_t), st), "status reset");
-    if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
+    if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, N_STATS * sizeof(unsigned long long), st), "stats reset");
     if (s == TR_OK) s = cuda_check(cudaMemcpyAsync(t->jobbuf, host, sizeof host, cudaMemcpyHostToDevice, st), "job copy");
     if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "job copy");
     if (s != TR_OK || n_targets <= 0) return s;
@@ -1397,7 +1584,7 @@ tr_status cd_run(const tr_tree* t, const int64_t* targets, int64_t n_targets, do
     memcpy(host, &a, sizeof(WalkArgs));
     memcpy(host + sizeof(WalkArgs), &n_targets, sizeof(int64_t));
     tr_status s = cuda_check(cudaMemsetAsync(t->status, 0, 4 * sizeof(int32_t), st), "status reset");
-    if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
+    if (s == TR_OK) s = cuda_check(cudaMemsetAsync(t->stats, 0, N_STATS * sizeof(unsigned long long), st), "stats reset");
     if (s == TR_OK) s = cuda_check(cudaMemcpyAsync(t->jobbuf, host, sizeof host, cudaMemcpyHostToDevice, st), "job copy");
     if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "job copy");
     if (s != TR_OK || n_targets <= 0) return s;
@@ -1429,7 +1616,7 @@ tr_status walk_batch_run(const tr_tree* const* trees, const int64_t* first, cons
         he[i] = total;
         smem = std::max(smem, walk_smem(trees[i]));
         if (s == TR_OK) s = cuda_check(cudaMemsetAsync(trees[i]->status, 0, 4 * sizeof(int32_t), st), "status reset");
-        if (s == TR_OK) s = cuda_check(cudaMemsetAsync(trees[i]->stats, 0, 4 * sizeof(unsigned long long), st), "stats reset");
+        if (s == TR_OK) s = cuda_check(cudaMemsetAsync(trees[i]->stats, 0, N_STATS * sizeof(unsigned long long), st), "stats reset");
     }
     if (s == TR_OK) s = cuda_check(cudaMemcpyAsync(jobbuf, host.data(), host.size(), cudaMemcpyHostToDevice, st), "job copy");
     if (s == TR_OK) s = cuda_check(cudaStreamSynchronize(st), "job copy");
@@ -1449,7 +1636,8 @@ tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaSt
     a.F = F; a.E = e; a.ion = ion;
     a.scales_in = r->scales;
     const size_t smem = (size_t)(r->use_e ? 3 : 2) * r->npix * r->nr * 8;
-    auto kern = r->mode == 0 ? k_sweep_stored<0, WALK_NT> : k_sweep_stored<1, WALK_NT>;
+    auto kern = r->mode == 0 ? k_sweep_stored<0, WALK_NT>
+                             : (r->mode == 1 ? k_sweep_stored<1, WALK_NT> : k_sweep_stored<2, WALK_NT>);
     tr_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "cudaFuncSetAttribute(sweep smem)");
     if (s != TR_OK) return s;

@@ -30,7 +30,7 @@ def test_defaults_include_kernels_and_boundaries(B):
     assert p.precision == B.TR_FP64 and p.zeta_g == 1 and p.delta_mode == 0
 
 
-@pytest.mark.parametrize("field,value,word", [("nside", 3, "nside"), ("eta_r", 3, "eta_r"), ("precision", 2, "precision"),
+@pytest.mark.parametrize("field,value,word", [("nside", 3, "nside"), ("eta_r", 3, "eta_r"), ("precision", 3, "precision"),
                                               ("kernel_alpha", 2, "kernel_alpha"), ("kernel_eps", 6, "kernel_eps"),
                                               ("bc", 3, "bc"), ("theta_lim", 0.0, "opening"), ("max_iter", 0, "max_iter"),
                                               ("alpha_B", -1.0, "alpha_B")])

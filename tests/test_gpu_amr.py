@@ -2,10 +2,11 @@
 at up to three refinement levels, Sec. 2.1; N_PIX = 192 with the IF and Src
 refinements of the MAC, Sec. 2.4).
 
-Bars: bit-exact node topology, node masses and centres and accepted-node
-lists in FP64; cell flux within 1e-5 (FP64) and 1e-3 (FP32 moments + FP64
-sweep) away from the ionisation front; classification identical except next
-to the front (cells whose neighbourhood holds both classes).
+Bars: bit-exact node topology and FP64 node masses and centres; accepted
+node lists bit-exact in every form; cell flux within 1e-5 (FP64) and 1e-3
+(both FP32 forms) away from the ionisation front; classification identical
+except next to the front (cells whose neighbourhood holds both classes).
+No fraction of the cells is exempt.
 """
 import math
 
@@ -13,11 +14,12 @@ import numpy as np
 import pytest
 
 from helpers import amr_cells, amr_interior_mask, decode_id
+from oracle_pool import amr_neighbours, oracle_pass, sampled_check
 from workloads.amr import amr_cluster
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {0: 1e-5, 1: 1e-3}
+RTOL = {0: 1e-5, 1: 1e-3, 2: 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -140,13 +142,15 @@ def test_amr_topology_and_nodes(B, orc, make, precision):
         off += 8 ** level
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("theta,theta_src", [(0.5, 0.5), (0.3, 0.2)])
-def test_amr_walk_lists_and_bins_fp64(B, orc, theta, theta_src):
-    """Accepted-node lists bit-exact and ray bins to rounding, for targets
-    of every cell size (cell indices b * 512 + c)."""
+def test_amr_walk_lists_and_bins(B, orc, theta, theta_src, precision):
+    """Accepted-node lists bit-exact in both walks and ray bins to rounding
+    (FP64) or 2e-5 (FP32), for targets of every cell size (cell indices
+    b * 512 + c)."""
     import torch
     g = mid_amr(theta_lim=theta, theta_src=theta_src)
-    t = gpu_amr_tree(B, g, 0)
+    t = gpu_amr_tree(B, g, precision)
     corner, size = amr_cells(g)
     rng = np.random.default_rng(11)
     targets = np.unique(np.concatenate([rng.choice(np.flatnonzero(size == s), 8) for s in np.unique(size)]
@@ -164,17 +168,18 @@ def test_amr_walk_lists_and_bins_fp64(B, orc, theta, theta_src):
     a, e, ids, counts = a.cpu().numpy(), e.cpu().numpy(), ids.cpu().numpy(), counts.cpu().numpy()
     ot = orc.AmrTree(g)
     p = orc.params_for(g)
+    tol = 1e-12 if precision == 0 else 2e-5
     for k, tgt in enumerate(targets):
         res = ot.walk(p, int(tgt))
         assert counts[k] == res["n_accepted"]
         assert np.array_equal(np.sort(ids[k, :counts[k]]), np.sort(res["accepted"]))
         scale = max(res["alpha"].max(), 1e-300)
-        np.testing.assert_allclose(a[k], res["alpha"], rtol=1e-12, atol=1e-12 * scale)
+        np.testing.assert_allclose(a[k], res["alpha"], rtol=tol, atol=tol * scale)
         escale = max(res["eps"].max(), 1e-300)
-        np.testing.assert_allclose(e[k], res["eps"], rtol=1e-12, atol=1e-12 * escale)
+        np.testing.assert_allclose(e[k], res["eps"], rtol=tol, atol=tol * escale)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_amr_solve_matches_oracle(B, orc, precision):
     """Every cell of the small AMR grid (18,432 cells, N_PIX = 192)."""
     g = small_amr()
@@ -184,19 +189,20 @@ def test_amr_solve_matches_oracle(B, orc, precision):
     np.testing.assert_allclose(e, F * g.hnu / 2.99792458e10, rtol=1e-14)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_amr_mid_sampled(B, orc, precision):
-    """The 64^3-finest grid with cells of three sizes, sampled targets."""
+    """The 64^3-finest grid with cells of three sizes: sampled targets and
+    their face neighbours against the oracle, every sampled cell away from
+    the oracle's front held to the bar."""
     g = mid_amr()
     F, e, ion = gpu_amr_solve(B, g, precision)
     rng = np.random.default_rng(5)
-    targets = rng.choice(g.n_leaves, 600, replace=False)
-    F_orc, _, ion_orc = orc.AmrTree(g).solve_pass(orc.params_for(g), targets=targets)
-    inner = amr_interior_mask(g, ion)[targets]
-    lit = inner & (F_orc > 0)
-    err = np.abs(F[targets][lit] - F_orc[lit]) / F_orc[lit]
-    assert err.max() <= RTOL[precision], np.sort(err)[-5:]
-    assert np.all(ion[targets][inner] == ion_orc[inner])
+    targets = rng.choice(g.n_leaves, 300, replace=False)
+    ot = orc.AmrTree(g)
+    p = orc.params_for(g)
+    checked, worst = sampled_check(F, ion, targets, amr_neighbours(g, targets),
+                                   lambda c: ot.solve_pass(p, targets=c), RTOL[precision])
+    assert checked >= 150
 
 
 def test_amr_if_mac_with_previous_pass(B, orc):
@@ -209,7 +215,7 @@ def test_amr_if_mac_with_previous_pass(B, orc):
     compare_amr(g, F, ion, F_orc, ion_orc, RTOL[0])
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_amr_unfused_equals_fused(B, precision):
     import torch
     g = small_amr(theta_src=0.3)
@@ -280,18 +286,17 @@ def test_amr_layout_errors(B):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", [1, 0])
-def test_full_size_amr_cluster_sampled(B, orc, precision):
+@pytest.mark.parametrize("precision", [1, 2, 0])
+def test_full_size_amr_cluster_sampled(B, precision):
     """The AMR cluster at full size (base 64^3 refined twice, 5.9M cells,
-    N_PIX = 192, N_R = 59, theta_IF = theta_src = 0.5), sampled targets one by
-    one against the oracle."""
+    N_PIX = 192, N_R = 59, theta_IF = theta_src = 0.5): sampled targets and
+    their face neighbours against the oracle; every sampled cell away from
+    the oracle's front meets the bar."""
     g = amr_cluster()
     F, e, ion = gpu_amr_solve(B, g, precision)
-    rng = np.random.default_rng(2105)
-    targets = rng.choice(g.n_leaves, 60, replace=False)
-    F_orc, _, ion_orc = orc.AmrTree(g).solve_pass(orc.params_for(g), targets=targets)
-    lit = F_orc > 0
-    err = np.abs(F[targets][lit] - F_orc[lit]) / F_orc[lit]
-    assert np.mean(err <= RTOL[precision]) >= 0.97, np.sort(err)[-5:]
-    assert np.mean(ion[targets] == ion_orc) >= 0.97
     assert np.all(np.isfinite(F))
+    rng = np.random.default_rng(2105)
+    targets = rng.choice(g.n_leaves, 40, replace=False).astype(np.int64)
+    checked, worst = sampled_check(F, ion, targets, amr_neighbours(g, targets),
+                                   lambda c: oracle_pass("amr", {}, c, nproc=8), RTOL[precision])
+    assert checked >= 20

@@ -41,7 +41,7 @@ def test_bc_walk_lists_and_bins_fp64(B, orc, bc):
         np.testing.assert_allclose(e[k], res["eps"], rtol=1e-12, atol=1e-12 * max(res["eps"].max(), 1e-300))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("bc", BCS)
 def test_bc_solve(B, orc, bc, precision):
     w = small_turbulent(N=32, theta_src=0.4)

@@ -58,10 +58,11 @@ def gpu_iterate(B, w, precision, max_iter, eps_lim, e_init=None):
     return F.cpu().numpy().ravel(), e.cpu().numpy().ravel(), ion.cpu().numpy().ravel(), it, dl
 
 
-@pytest.mark.parametrize("precision,rtol", [(0, 1e-5), (1, 1e-3)])
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-5), (1, 1e-3), (2, 1e-3)])
 def test_fixed_passes_match_oracle(B, orc, precision, rtol):
     """Four passes (eps_lim = 0 never stops early): IF MAC and zeta_d are live
-    from the second pass on."""
+    from the second pass on.  Every cell away from the front meets the bar
+    (the FP32 forms decide the IF MAC on the FP64 masses)."""
     w = small()
     F, e, ion, it, dl = gpu_iterate(B, w, precision, 4, 0.0)
     Fo, eo, iono, ito, dlo = orc.solve(w, orc.params_for(w), max_iter=4, eps_lim=0.0)
@@ -69,8 +70,9 @@ def test_fixed_passes_match_oracle(B, orc, precision, rtol):
     inner = interior_mask(iono.reshape(w.N, w.N, w.N)).ravel()
     assert np.array_equal(ion[inner], iono[inner])
     lit = inner & (Fo > 0)
-    frac_ok = np.mean(np.abs(F[lit] - Fo[lit]) <= rtol * Fo[lit])
-    assert frac_ok >= (1.0 if precision == 0 else 0.99), frac_ok
+    err = np.abs(F[lit] - Fo[lit]) / Fo[lit]
+    assert err.max() <= rtol, np.sort(err)[-5:]
+    assert np.all(F[inner & (Fo == 0)] == 0.0)
     assert dl == pytest.approx(dlo, rel=1e-3 if precision else 1e-6)
 
 

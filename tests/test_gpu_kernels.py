@@ -1,12 +1,10 @@
 """Parity of the radial kernel choices (App. A) between the CUDA path and
 the oracle: W_p / W_g for alpha and e; W_f,3, W_f,1, W_f,2, generalised
 W_f,3, W_p, W_g for eps.  Same bars as the default kernels: ray bins within
-1e-12 in FP64, cell flux within 1e-5 (FP64) / 1e-3 (FP32 form) away from
+1e-12 in FP64, cell flux within 1e-5 (FP64) / 1e-3 (FP32 forms) away from
 the ionisation front."""
 import numpy as np
 import pytest
-
-from helpers import interior_mask
 
 from test_gpu_parity import B, RTOL, compare_fields, dev, gpu_solve, gpu_tree, small_turbulent  # noqa: F401
 
@@ -39,27 +37,17 @@ def test_kernel_bins_fp64(B, orc, kernel_alpha, kernel_eps):
         np.testing.assert_allclose(e[k], res["eps"], rtol=1e-12, atol=1e-12 * max(res["eps"].max(), 1e-300))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("kernel_alpha,kernel_eps", COMBOS)
 def test_kernel_solve(B, orc, precision, kernel_alpha, kernel_eps):
-    """The FP32 form takes its MAC decisions in FP32, so a node within
-    rounding of theta_src can be opened on one side and accepted on the
-    other.  The flux kernels make such a flip invisible at the target (each
-    level delivers the exact point-source flux); W_p and W_g for eps do not
-    conserve the flux, so there a flip shows in F at the per-cent level:
-    for them a flip-sized fraction (0.5%) of cells may miss the FP32 bar."""
+    """Every kernel choice in every form against the oracle, no cell exempt
+    but the front band: the FP32 forms take their opening decisions, and the
+    choices of the radial spreading that jump with the distance, in FP64
+    where FP32 cannot settle them."""
     w = small_turbulent(N=32, theta_src=0.6)
     kw = dict(kernel_alpha=kernel_alpha, kernel_eps=kernel_eps)
     F, e, ion = gpu_solve(B, w, precision, **kw)
     F_orc, _, ion_orc = orc.Tree(w).solve_pass(orc.params_for(w, **kw))
-    if precision == 1 and kernel_eps in (4, 5):
-        inner = interior_mask(ion_orc.reshape((w.N,) * 3)).ravel()
-        assert not np.any((ion != ion_orc) & inner)
-        lit = inner & (F_orc > 0)
-        err = np.abs(F[lit] - F_orc[lit]) / F_orc[lit]
-        assert np.mean(err <= RTOL[1]) >= 0.995, np.sort(err)[-5:]
-        assert err.max() < 0.05
-        return
     compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision])
 
 
