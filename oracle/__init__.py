@@ -23,7 +23,9 @@ _lock = threading.Lock()
 _lib = None
 
 TQH, TQ, TB, TM = 16, 33, 40, 8
-NKEYS = 6 * TQ * TQ * TB
+TW = 2 * TM ** 3                       # weight denominator of a table entry's counts
+NFACEKEYS, NEDGEKEYS, NCORNERKEYS = 6 * TQ * TQ * TB, 12 * TQ * TB, 8 * TB
+NKEYS = NFACEKEYS + NEDGEKEYS + NCORNERKEYS
 
 
 def build(force: bool = False) -> str:
@@ -111,6 +113,8 @@ def lib():
             L.orc_column_density.argtypes = [C.c_void_p, C.POINTER(Params), C.c_int64, _D]
             L.orc_solve_pass.restype = C.c_int32
             L.orc_solve_pass.argtypes = [C.c_void_p, C.POINTER(Params), _I64, C.c_int64, _D, _D, _U8]
+            L.orc_free_flux.restype = C.c_int32
+            L.orc_free_flux.argtypes = [C.c_void_p, C.POINTER(Params), _I64, C.c_int64, _D]
             L.orc_solve.restype = C.c_int32
             L.orc_solve.argtypes = [C.POINTER(Params), _D, _D, _D, C.c_int32, _D, _D, _D,
                                     C.c_int32, C.c_double, C.c_int32, _D, _D, _U8, _I32, _D]
@@ -236,6 +240,8 @@ class Tree:
     """Oracle octree over a uniform N^3 grid (Sec. 2.1)."""
 
     def __init__(self, w, e_prev=None, box_lo=(0.0, 0.0, 0.0)):
+        if w.N < 2 or w.N & (w.N - 1):
+            raise ValueError(f"the octree needs a power-of-two grid (got N = {w.N})")
         self.N = w.N
         self._keep = [_f64(w.n_H).ravel(), _f64(w.ndot_cell).ravel() if w.ndot_cell is not None else None,
                       _f64(w.src_xyz).reshape(-1), _f64(w.src_Q), _f64(e_prev).ravel() if e_prev is not None else None,
@@ -302,6 +308,17 @@ class Tree:
         F, e, ion = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.uint8)
         lib().orc_solve_pass(self.h, C.byref(p), tp, n, _p(F), _p(e), _p(ion, _U8))
         return F, e, ion
+
+    def free_flux(self, p: Params, targets=None):
+        """Flux each target would get with no recombination losses."""
+        if targets is None:
+            n, tp = self.n_leaf, None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            n, tp = targets.shape[0], _p(targets, _I64)
+        F = np.zeros(n)
+        lib().orc_free_flux(self.h, C.byref(p), tp, n, _p(F))
+        return F
 
 
 class AmrTree(Tree):

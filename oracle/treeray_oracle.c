@@ -26,6 +26,13 @@
  *     fraction of ORC_TM^3 sample points of the cube that fall in HEALPix
  *     pixel k, for a representative cube chosen by an integer key of the
  *     node's geometric-centre offset (cube-map face, (u,v) bin, psi = h/d bin).
+ *     A node whose offset ties between two (three) axes for the largest
+ *     component gets an edge (corner) key with its representative direction
+ *     on that edge (corner); where that direction lies on a plane x = +-y,
+ *     each sample counts half in its pixel and half in the mirror pixel, so
+ *     that the table -- and the radiation field of a mirror-symmetric scene
+ *     (Sec. 3.4: symmetric about x = y) -- keeps the mirror symmetries of
+ *     the HEALPix pixels.
  *  R5 W_p (Eq. A2): the printed outer branch violates its own constraints;
  *     it is rebuilt from them: W_p2(x) = (x - sqrt3/2)^2 (a2 x + 2A(2+sqrt3) - a2/2)
  *     with the printed a1, a2, A, M.  W_p is used in |x| and normalised over
@@ -356,14 +363,10 @@ int32_t orc_table_key(int64_t ox, int64_t oy, int64_t oz, int64_t s)
 {
     int64_t o[3] = {ox, oy, oz};
     int64_t ab[3] = {llabs(ox), llabs(oy), llabs(oz)};
-    int a = 0;                                  /* dominant axis, ties to the lowest */
-    if (ab[1] > ab[a]) a = 1;
-    if (ab[2] > ab[a]) a = 2;
-    int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
-    int64_t A = ab[a];
-    int face = 2 * a + (o[a] < 0 ? 1 : 0);
-    int64_t u = face_bin(o[b], A);
-    int64_t v = face_bin(o[c], A);
+    int64_t A = ab[0];
+    if (ab[1] > A) A = ab[1];
+    if (ab[2] > A) A = ab[2];
+    int ntie = (ab[0] == A) + (ab[1] == A) + (ab[2] == A);
     /* psi = h / |centre offset| = 2s / |o|; bin = floor(32 psi) */
     int64_t o2 = ox * ox + oy * oy + oz * oz;
     int64_t lim = 64 * s, lim2 = lim * lim;
@@ -371,25 +374,84 @@ int32_t orc_table_key(int64_t ox, int64_t oy, int64_t oz, int64_t s)
     while (pb > 0 && pb * pb * o2 > lim2) pb--;
     while ((pb + 1) * (pb + 1) * o2 <= lim2) pb++;
     if (pb > ORC_TB - 1) pb = ORC_TB - 1;
-    return (int32_t)(((face * ORC_TQ + u) * ORC_TQ + v) * ORC_TB + pb);
+    if (ntie == 1) {                            /* face of the dominant axis */
+        int a = (ab[0] == A) ? 0 : ((ab[1] == A) ? 1 : 2);
+        int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+        int face = 2 * a + (o[a] < 0 ? 1 : 0);
+        int64_t u = face_bin(o[b], A);
+        int64_t v = face_bin(o[c], A);
+        return (int32_t)(((face * ORC_TQ + u) * ORC_TQ + v) * ORC_TB + pb);
+    }
+    if (ntie == 2) {                            /* edge between the two tied faces */
+        int c = (ab[0] != A) ? 0 : ((ab[1] != A) ? 1 : 2);
+        int a = (c == 0) ? 1 : 0, b = (c == 2) ? 1 : 2;
+        int pair = (c == 2) ? 0 : ((c == 1) ? 1 : 2);           /* (0,1), (0,2), (1,2) */
+        int edge = 4 * pair + 2 * (o[a] < 0) + (o[b] < 0);
+        int64_t v = face_bin(o[c], A);
+        return (int32_t)(ORC_NFACEKEYS + (edge * ORC_TQ + v) * ORC_TB + pb);
+    }
+    int corner = (ox < 0) + 2 * (oy < 0) + 4 * (oz < 0);
+    return (int32_t)(ORC_NFACEKEYS + ORC_NEDGEKEYS + corner * ORC_TB + pb);
 }
 
 typedef struct { int32_t n; int32_t* pix; int32_t* cnt; } orc_entry;
 typedef struct { int32_t nside; orc_entry* e; } orc_table;
 static orc_table g_tables[16];   /* one lazily filled table per N_side */
 
+/* The representative direction of a key (not normalised) and its psi bin.
+ * *mirror = +1 or -1 for the keys whose direction lies on the plane x = y
+ * (resp. x = -y) -- edge keys of the x-y edges and corner keys -- and 0
+ * otherwise. */
+static void key_geometry(int32_t key, double p[3], int32_t* pb, int* mirror)
+{
+    *pb = key % ORC_TB;
+    *mirror = 0;
+    if (key < ORC_NFACEKEYS) {
+        int32_t rest = key / ORC_TB;
+        int32_t v = rest % ORC_TQ; rest /= ORC_TQ;
+        int32_t u = rest % ORC_TQ;
+        int32_t face = rest / ORC_TQ;
+        int a = face / 2;
+        int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+        p[a] = (face & 1) ? -1.0 : 1.0;
+        p[b] = face_coord(u);
+        p[c] = face_coord(v);
+        return;
+    }
+    if (key < ORC_NFACEKEYS + ORC_NEDGEKEYS) {
+        int32_t rest = (key - ORC_NFACEKEYS) / ORC_TB;
+        int32_t v = rest % ORC_TQ;
+        int32_t edge = rest / ORC_TQ;
+        int pair = edge / 4;
+        int a = (pair == 2) ? 1 : 0, b = (pair == 0) ? 1 : 2, c = 3 - a - b;
+        double sa = (edge & 2) ? -1.0 : 1.0, sb = (edge & 1) ? -1.0 : 1.0;
+        p[a] = sa; p[b] = sb; p[c] = face_coord(v);
+        if (pair == 0) *mirror = (sa == sb) ? 1 : -1;
+        return;
+    }
+    int32_t corner = (key - ORC_NFACEKEYS - ORC_NEDGEKEYS) / ORC_TB;
+    p[0] = (corner & 1) ? -1.0 : 1.0;
+    p[1] = (corner & 2) ? -1.0 : 1.0;
+    p[2] = (corner & 4) ? -1.0 : 1.0;
+    *mirror = (p[0] == p[1]) ? 1 : -1;
+}
+
+/* The pixel that the reflection through the plane x = t y (t = +-1) maps
+ * pixel k to: HEALPix has that symmetry, so the image of the pixel's centre
+ * is the centre of its mirror pixel. */
+static int64_t mirror_pixel(int32_t nside, int64_t k, int t)
+{
+    double v[3];
+    orc_pix2vec(nside, k, v);
+    return orc_ang2pix(nside, t * v[1], t * v[0], v[2]);
+}
+
 static void compute_entry(int32_t nside, int32_t key, orc_entry* out)
 {
-    int32_t pb = key % ORC_TB, rest = key / ORC_TB;
-    int32_t v = rest % ORC_TQ; rest /= ORC_TQ;
-    int32_t u = rest % ORC_TQ;
-    int32_t face = rest / ORC_TQ;
-    int a = face / 2;
-    int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
     double p[3];
-    p[a] = (face & 1) ? -1.0 : 1.0;
-    p[b] = face_coord(u);
-    p[c] = face_coord(v);
+    int32_t pb;
+    int mirror;
+    key_geometry(key, p, &pb, &mirror);
     double n = sqrt((p[0] * p[0] + p[1] * p[1]) + p[2] * p[2]);
     double C[3] = {p[0] / n, p[1] / n, p[2] / n};
     double psi = ((double)pb + 0.5) / 32.0;
@@ -401,10 +463,13 @@ static void compute_entry(int32_t nside, int32_t key, orc_entry* out)
                 double fx = (ix + 0.5) / ORC_TM - 0.5;
                 double fy = (iy + 0.5) / ORC_TM - 0.5;
                 double fz = (iz + 0.5) / ORC_TM - 0.5;
-                double qx = C[0] + psi * fx;
-                double qy = C[1] + psi * fy;
-                double qz = C[2] + psi * fz;
-                hist[orc_ang2pix(nside, qx, qy, qz)]++;
+                int64_t k = orc_ang2pix(nside, C[0] + psi * fx, C[1] + psi * fy, C[2] + psi * fz);
+                if (mirror) {                   /* half to the pixel, half to its mirror */
+                    hist[k] += 1;
+                    hist[mirror_pixel(nside, k, mirror)] += 1;
+                } else {
+                    hist[k] += 2;
+                }
             }
     int32_t n_nz = 0;
     for (int64_t k = 0; k < npix; ++k) n_nz += hist[k] > 0;
@@ -493,6 +558,7 @@ orc_tree* orc_tree_build(int32_t N, double dx_cm, double alpha_B, const double* 
                          int32_t nsrc, const double* src_xyz_cm, const double* src_Q,
                          const double* e_prev)
 {
+    if (N < 2 || (N & (N - 1)) != 0) return NULL;   /* the octree needs a power-of-two grid */
     orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
     int32_t L = 0;
     while ((1 << L) < N) L++;
@@ -820,7 +886,7 @@ static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t
         node_frame(w, level, ix, iy, iz, o, tc);
         const orc_entry* ent = table_entry(p->nside, orc_table_key(o[0], o[1], o[2], (int64_t)(w->t->N >> level)));
         double omega = 4.0 * ORC_PI / (double)(12 * (int64_t)p->nside * p->nside);
-        const double inv_m3 = 1.0 / (double)(ORC_TM * ORC_TM * ORC_TM);
+        const double inv_m3 = 1.0 / (double)ORC_TW;
         for (int32_t j = 0; j < ent->n; ++j)
             w->cd[ent->pix[j]] += ((double)ent->cnt[j] * inv_m3) * nd->m / (omega * (d * d));
         return;
@@ -838,7 +904,7 @@ static void map_node(walk_ctx* w, int32_t level, int64_t ix, int64_t iy, int64_t
     if (nd->alpha != 0.0) smooth_weights(p->kernel_alpha == ORC_K_WG, d, h, nr, p->eta_r, w->wa);
     if (nd->eps != 0.0) orc_eps_weights(p->kernel_eps, d, h, nr, p->eta_r, w->we);
     if (use_e && nd->e != 0.0) smooth_weights(p->kernel_alpha == ORC_K_WG, d, h, nr, p->eta_r, w->wee);
-    const double inv_m3 = 1.0 / (double)(ORC_TM * ORC_TM * ORC_TM);
+    const double inv_m3 = 1.0 / (double)ORC_TW;
     for (int32_t j = 0; j < ent->n; ++j) {
         double wk = (double)ent->cnt[j] * inv_m3;     /* volume fraction in ray k */
         int64_t k = ent->pix[j];
@@ -1060,6 +1126,43 @@ int32_t orc_solve_pass(const orc_tree* t, const orc_params* p, const int64_t* ta
         if (ion_out) ion_out[q] = (uint8_t)(F > 0.0);
     }
     free(ba); free(be); free(bee); free(av); free(ev); free(vol);
+    return 0;
+}
+
+/* The flux each target would receive if nothing were absorbed: the photon
+ * rates on its rays taken to the target unattenuated, sum_k sum_j
+ * (eps_kj / 4 pi) / r_j^2, plus its own emission (R3); photons s^-1 cm^-2.
+ * F_free - F is the flux the recombinations removed: a rounding error of
+ * relative size u in the recombination terms moves F by about u times it,
+ * which is how the tests judge reduced-precision results near a front. */
+int32_t orc_free_flux(const orc_tree* t, const orc_params* p, const int64_t* targets,
+                      int64_t n_targets, double* F_free_out)
+{
+    double lray = lray_of(p);
+    int32_t nr = orc_num_points(p->eta_r, lray);
+    int64_t npix = 12 * (int64_t)p->nside * p->nside;
+    int64_t nbin = npix * nr;
+    double* ba = (double*)malloc(sizeof(double) * (size_t)nbin);
+    double* be = (double*)malloc(sizeof(double) * (size_t)nbin);
+    double dx2 = t->dx_cm * t->dx_cm;
+    int64_t n = targets ? n_targets : t->n_leaf;
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t tgt = targets ? targets[q] : q;
+        orc_walk_target(t, p, tgt, ba, be, NULL, NULL, 0, NULL);
+        double F = 0.0;
+        for (int64_t k = 0; k < npix; ++k)
+            for (int32_t j = 1; j < nr; ++j) {
+                double rj = orc_radius(j, p->eta_r);
+                F += be[k * nr + j] / (4.0 * ORC_PI) / (rj * rj);
+            }
+        int32_t tl;
+        int64_t p3[3], edge;
+        target_geom(t, tgt, &tl, p3, &edge);
+        double rtp = 0.5 * (double)edge;
+        F += t->eps_c[tgt] / (4.0 * ORC_PI * (rtp * rtp));
+        F_free_out[q] = F / dx2;
+    }
+    free(ba); free(be);
     return 0;
 }
 

@@ -18,12 +18,24 @@ extern "C" {
 #endif
 
 /* Node->ray table resolution (the paper's table is defined in Paper I, not
- * reproduced; this oracle samples each node cube with ORC_TM^3 points). */
+ * reproduced; this oracle samples each node cube with ORC_TM^3 points).
+ * Keys: a face key when one axis dominates the node offset, an edge key
+ * when two axes tie for the largest |offset|, a corner key when all three
+ * do; an edge or corner key's representative direction lies exactly on the
+ * edge or corner.  A key's weights are counts out of ORC_TW: each sample
+ * point counts 2, or, for the keys whose direction lies on a plane x = +-y
+ * (a symmetry plane of HEALPix), 1 in its pixel and 1 in that pixel's
+ * mirror image, so that the table keeps the mirror symmetries that the
+ * HEALPix pixels have. */
 #define ORC_TQH 16  /* face bins on either side of the face centre */
 #define ORC_TQ 33   /* (u,v) bins per cube-map face axis: 2*ORC_TQH + centre bin */
 #define ORC_TB 40   /* psi = h/d bins of width 1/32 */
 #define ORC_TM 8    /* sample points per axis */
-#define ORC_NKEYS (6 * ORC_TQ * ORC_TQ * ORC_TB)
+#define ORC_TW (2 * ORC_TM * ORC_TM * ORC_TM)   /* weight denominator */
+#define ORC_NFACEKEYS (6 * ORC_TQ * ORC_TQ * ORC_TB)
+#define ORC_NEDGEKEYS (12 * ORC_TQ * ORC_TB)
+#define ORC_NCORNERKEYS (8 * ORC_TB)
+#define ORC_NKEYS (ORC_NFACEKEYS + ORC_NEDGEKEYS + ORC_NCORNERKEYS)
 
 typedef struct {
     int32_t N;            /* cells per axis, power of two >= 2 */
@@ -111,6 +123,10 @@ void orc_column_density(const orc_tree* t, const orc_params* p, int64_t target, 
 
 int32_t orc_solve_pass(const orc_tree* t, const orc_params* p, const int64_t* targets,
                        int64_t n_targets, double* F_out, double* e_out, uint8_t* ion_out);
+
+/* unattenuated flux of each target (no recombination losses), cm^-2 s^-1 */
+int32_t orc_free_flux(const orc_tree* t, const orc_params* p, const int64_t* targets,
+                      int64_t n_targets, double* F_free_out);
 
 /* full iteration (Sec. 2.6): passes until delta < eps_lim or max_iter.
  * delta_mode 0 = per cell (Eq. 21), 1 = total (Eq. 20). */

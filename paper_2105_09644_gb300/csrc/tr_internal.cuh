@@ -17,12 +17,20 @@ namespace tr {
 
 // ---- node->ray table definition (Sec. 2.3; the paper's table comes from
 // Paper I and is not reproduced: a node is an axis-aligned cube sampled with
-// TM^3 points, keyed by the integer offset of its geometric centre) ---------
+// TM^3 points, keyed by the integer offset of its geometric centre; ties
+// between axes have keys of their own so that the table keeps the mirror
+// symmetries of the HEALPix pixels) -----------------------------------------
 constexpr int TQH = 16;                     // face bins on either side of the face centre
 constexpr int TQ = 2 * TQH + 1;             // face bins per axis, centre bin included
 constexpr int TB = 40;                      // psi = h/d bins of width 1/32
 constexpr int TM = 8;                       // sample points per cube axis
-constexpr int NKEYS = 6 * TQ * TQ * TB;
+constexpr int TW = 2 * TM * TM * TM;        // weight denominator of an entry's count
+// keys: face keys (one axis dominates the node offset), edge keys (two axes
+// tie for the largest |offset|), corner keys (all three tie)
+constexpr int NFACEKEYS = 6 * TQ * TQ * TB;
+constexpr int NEDGEKEYS = 12 * TQ * TB;
+constexpr int NCORNERKEYS = 8 * TB;
+constexpr int NKEYS = NFACEKEYS + NEDGEKEYS + NCORNERKEYS;
 constexpr int MAX_LEVELS = 10;              // N <= 512
 constexpr int MAX_NR = 128;
 constexpr double PI_D = 3.14159265358979323846;
@@ -80,7 +88,7 @@ struct SweepTables {                        // depend on (N_R, eta_R, N_side, N_
     double* inv_r2 = nullptr;               // 1/r_j^2 (0 for j = 0)
     double* inv_vol = nullptr;              // 1 / ray-cell volume (cells^-3), 4pi/N_PIX shells
     float* inv_volf = nullptr;              // the same in FP32
-    double* G = nullptr;                    // [i][j] dV_ij zeta_g,ij (Eq. 15-16)
+    double* G = nullptr;                    // [i][j] (1/2) dV_ij zeta_g,ij (Eq. 14-16)
     double* ID2 = nullptr;                  // [i][j] 1/(r_j - r_mid,i)^2
     double* GI = nullptr;                   // [i][j] G_ij ID2_ij
     float* Gf = nullptr;                    // FP32 copies of G, ID2, GI

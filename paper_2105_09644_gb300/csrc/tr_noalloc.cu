@@ -16,7 +16,7 @@ constexpr int NA_MAX_N = 32;                     // grids up to 32^3 cells
 constexpr int NA_MAX_NSIDE = 2;                  // up to N_PIX = 48 rays
 constexpr int64_t NA_NCELL = (int64_t)NA_MAX_N * NA_MAX_N * NA_MAX_N;
 constexpr int64_t NA_NNODES = 37449;             // (8^6 - 1) / 7 nodes of a 32^3 octree
-constexpr uint32_t NA_ENT_CAP = 1700000;         // node->ray table entries (N_side 2 needs 1,649,096)
+constexpr uint32_t NA_ENT_CAP = 1800000;         // node->ray table entries (N_side 2 needs 1,748,216)
 constexpr size_t NR2 = (size_t)MAX_NR * MAX_NR;
 
 constexpr size_t up(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -9,11 +9,16 @@
 // node's geometric centre and the target centre (in half cells): cube-map
 // face of the dominant axis, a mirror-symmetric bin of each of the other two
 // face coordinates, and the bin floor(32 psi) of psi = node size / centre
-// distance.  Each key's weights are those of a representative cube at
-// distance 1 in the bin's central direction with psi at the bin centre.
+// distance.  Offsets whose largest component is shared by two axes (three
+// axes) have edge (corner) keys whose representative direction lies on that
+// cube edge (corner).  Each key's weights are those of a representative cube
+// at distance 1 in the key's direction with psi at the bin centre.  Every
+// sample counts 2 out of TW = 2 TM^3; for keys whose direction lies on a
+// plane x = +-y (a mirror plane of the HEALPix pixels) a sample counts 1 in
+// its pixel and 1 in the mirror pixel, so the table has those symmetries.
 //
 // Storage is CSR: ent[off[k] .. off[k+1]) holds (pixel << 16) | count,
-// sorted by pixel; the weight is count / TM^3.
+// sorted by pixel; the weight is count / TW.
 #include <map>
 #include <mutex>
 #include <utility>
@@ -67,22 +72,87 @@ __device__ double face_coord(int u) {
     return -(2.0 * (double)(TQH - 1 - u) + 1.0) / (2.0 * TQH);
 }
 
-// Histogram of the key's representative cube over the pixels (block-wide).
+// Centre of ring-scheme pixel k as (z, phi) (Gorski et al. 2005): rings are
+// numbered from the north pole; a polar-cap ring i holds 4i pixels, an
+// equatorial ring 4 N_side, every other one of them shifted by half a pixel.
+__device__ void pix_centre(int nside, int k, double& z, double& phi) {
+    const int npix = 12 * nside * nside, ncap = 2 * nside * (nside - 1);
+    const double ns = (double)nside;
+    if (k < ncap) {                                          // north cap
+        int i = (int)floor(0.5 * (1.0 + sqrt(1.0 + 2.0 * (double)k)));
+        while (2 * i * (i - 1) > k) --i;
+        while (2 * (i + 1) * i <= k) ++i;
+        const int j = k - 2 * i * (i - 1);                   // 0-based in the ring
+        z = 1.0 - (double)(i * i) / (3.0 * ns * ns);
+        phi = ((double)j + 0.5) * 0.5 * PI_D / (double)i;
+    } else if (k < npix - ncap) {                            // equatorial belt
+        const int q = k - ncap;
+        const int i = q / (4 * nside) + nside;               // ring N .. 3N
+        const int j = q % (4 * nside);
+        const double shift = ((i - nside) & 1) ? 0.0 : 0.5;
+        z = (2.0 * ns - (double)i) * 2.0 / (3.0 * ns);
+        phi = ((double)j + shift) * 0.5 * PI_D / ns;
+    } else {                                                 // south cap, mirror of the north
+        const int q = npix - 1 - k;
+        int i = (int)floor(0.5 * (1.0 + sqrt(1.0 + 2.0 * (double)q)));
+        while (2 * i * (i - 1) > q) --i;
+        while (2 * (i + 1) * i <= q) ++i;
+        const int jr = q - 2 * i * (i - 1);                  // 0-based from the ring's end
+        z = -(1.0 - (double)(i * i) / (3.0 * ns * ns));
+        phi = ((double)(4 * i - 1 - jr) + 0.5) * 0.5 * PI_D / (double)i;
+    }
+}
+
+// The pixel that the reflection through the plane x = t y (t = +-1) maps
+// pixel k to: the pixel of the mirrored centre (HEALPix has the symmetry).
+__device__ int mirror_pixel(int nside, int k, double t) {
+    double z, phi;
+    pix_centre(nside, k, z, phi);
+    const double st = sqrt((1.0 - z) * (1.0 + z));
+    const double x = st * cos(phi), y = st * sin(phi);
+    return ang2pix_ring(nside, t * y, t * x, z);
+}
+
+// Representative direction of a key (not normalised) and whether it lies on
+// a plane x = +-y (mirror = +-1) or not (0).
+__device__ void key_direction(int key, double* p, int& mirror) {
+    mirror = 0;
+    if (key < NFACEKEYS) {
+        int rest = key / TB;
+        const int v = rest % TQ;
+        rest /= TQ;
+        const int u = rest % TQ;
+        const int face = rest / TQ;
+        const int a = face / 2, b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+        p[a] = (face & 1) ? -1.0 : 1.0;
+        p[b] = face_coord(u);
+        p[c] = face_coord(v);
+    } else if (key < NFACEKEYS + NEDGEKEYS) {
+        const int rest = (key - NFACEKEYS) / TB;
+        const int v = rest % TQ, edge = rest / TQ, pair = edge / 4;
+        const int a = (pair == 2) ? 1 : 0, b = (pair == 0) ? 1 : 2, c = 3 - a - b;
+        const double sa = (edge & 2) ? -1.0 : 1.0, sb = (edge & 1) ? -1.0 : 1.0;
+        p[a] = sa; p[b] = sb; p[c] = face_coord(v);
+        if (pair == 0) mirror = sa == sb ? 1 : -1;
+    } else {
+        const int corner = (key - NFACEKEYS - NEDGEKEYS) / TB;
+        p[0] = (corner & 1) ? -1.0 : 1.0;
+        p[1] = (corner & 2) ? -1.0 : 1.0;
+        p[2] = (corner & 4) ? -1.0 : 1.0;
+        mirror = p[0] == p[1] ? 1 : -1;
+    }
+}
+
+// Histogram of the key's representative cube over the pixels (block-wide),
+// in counts out of TW.
 __device__ void key_histogram(int nside, int key, int* hist) {
     const int npix = 12 * nside * nside;
     for (int k = threadIdx.x; k < npix; k += blockDim.x) hist[k] = 0;
     __syncthreads();
-    int pb = key % TB, rest = key / TB;
-    int v = rest % TQ;
-    rest /= TQ;
-    int u = rest % TQ;
-    int face = rest / TQ;
-    int a = face / 2;
-    int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    const int pb = key % TB;
     double p[3];
-    p[a] = (face & 1) ? -1.0 : 1.0;
-    p[b] = face_coord(u);
-    p[c] = face_coord(v);
+    int mirror;
+    key_direction(key, p, mirror);
     double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(p[0], p[0]), __dmul_rn(p[1], p[1])),
                                     __dmul_rn(p[2], p[2])));
     double C0 = __ddiv_rn(p[0], n), C1 = __ddiv_rn(p[1], n), C2 = __ddiv_rn(p[2], n);
@@ -95,7 +165,13 @@ __device__ void key_histogram(int nside, int key, int* hist) {
         double qx = __dadd_rn(C0, __dmul_rn(psi, fx));
         double qy = __dadd_rn(C1, __dmul_rn(psi, fy));
         double qz = __dadd_rn(C2, __dmul_rn(psi, fz));
-        atomicAdd(&hist[ang2pix_ring(nside, qx, qy, qz)], 1);
+        const int k = ang2pix_ring(nside, qx, qy, qz);
+        if (mirror) {
+            atomicAdd(&hist[k], 1);
+            atomicAdd(&hist[mirror_pixel(nside, k, (double)mirror)], 1);
+        } else {
+            atomicAdd(&hist[k], 2);
+        }
     }
     __syncthreads();
 }

@@ -313,8 +313,10 @@ __global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, 
 }
 
 // Ray constants: r_i (Eq. 4), ray-cell volumes, and for each segment i and
-// source point j > i the loss geometry dV_ij zeta_g,ij (Eq. 15-16) and the
-// inverse square distance from j to the segment midpoint.
+// source point j > i the loss geometry (1/2) dV_ij zeta_g,ij (Eq. 14-16: the
+// 1/2 of the segment's mean coefficient, so that a sweep multiplies it by
+// alpha_i + alpha_{i+1}) and the inverse square distance from j to the
+// segment midpoint.
 __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g, double* r, float* rf,
                                double* inv_r2, double* inv_vol, float* inv_volf, double* G, double* ID2, double* GI,
                                float* Gf, float* ID2f, float* GIf) {
@@ -339,7 +341,7 @@ __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g,
             const double a = rj - ri, b = rj - ri1;
             const double dV = (a * a * a - b * b * b) / 3.0;
             const double zg = zeta_g ? fmin(1.0, (double)nside * (rj - ri) / (2.0 * rj)) : 1.0;
-            g = dV * zg;
+            g = 0.5 * dV * zg;
             const double rm = 0.5 * (ri + ri1);
             id2 = 1.0 / ((rj - rm) * (rj - rm));
         }

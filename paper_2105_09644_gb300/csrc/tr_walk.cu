@@ -168,24 +168,38 @@ __device__ __forceinline__ int face_bin(int x, int A) {
 }
 
 // Table key of a node from the integer offset o = 2 (node centre - target
-// centre) in half cells and the node edge s in cells.
+// centre) in half cells and the node edge s in cells: a face key when one
+// axis has the largest |o|, an edge key when two tie for it, a corner key
+// when all three do.
 __device__ __forceinline__ int table_key(int ox, int oy, int oz, int s) {
     const int ax = abs(ox), ay = abs(oy), az = abs(oz);
-    int a = 0, A = ax;
-    if (ay > A) { a = 1; A = ay; }
-    if (az > A) { a = 2; A = az; }
-    const int ob = (a == 0) ? oy : ox;
-    const int oc = (a == 2) ? oy : oz;
-    const int oa = (a == 0) ? ox : (a == 1 ? oy : oz);
-    const int face = 2 * a + (oa < 0 ? 1 : 0);
-    const int u = face_bin(ob, A), v = face_bin(oc, A);
+    const int A = max(ax, max(ay, az));
     const long long o2 = (long long)ox * ox + (long long)oy * oy + (long long)oz * oz;
     const long long lim = 64LL * s, lim2 = lim * lim;
     long long pb = (long long)((float)lim * rsqrtf((float)o2));
     while (pb > 0 && pb * pb * o2 > lim2) --pb;
     while ((pb + 1) * (pb + 1) * o2 <= lim2) ++pb;
     if (pb > TB - 1) pb = TB - 1;
-    return ((face * TQ + u) * TQ + v) * TB + (int)pb;
+    const int tx = ax == A, ty = ay == A, tz = az == A;
+    const int ntie = tx + ty + tz;
+    if (ntie == 1) {
+        const int a = tx ? 0 : (ty ? 1 : 2);
+        const int ob = (a == 0) ? oy : ox;
+        const int oc = (a == 2) ? oy : oz;
+        const int oa = (a == 0) ? ox : (a == 1 ? oy : oz);
+        const int face = 2 * a + (oa < 0 ? 1 : 0);
+        const int u = face_bin(ob, A), v = face_bin(oc, A);
+        return ((face * TQ + u) * TQ + v) * TB + (int)pb;
+    }
+    if (ntie == 2) {                         // edge of the tied axes a < b, the third axis c binned
+        const int c = !tx ? 0 : (!ty ? 1 : 2);
+        const int pair = c == 2 ? 0 : (c == 1 ? 1 : 2);
+        const int oa = c == 0 ? oy : ox, ob = c == 2 ? oy : oz, oc = c == 0 ? ox : (c == 1 ? oy : oz);
+        const int edge = 4 * pair + 2 * (oa < 0) + (ob < 0);
+        return NFACEKEYS + (edge * TQ + face_bin(oc, A)) * TB + (int)pb;
+    }
+    const int corner = (ox < 0) + 2 * (oy < 0) + 4 * (oz < 0);
+    return NFACEKEYS + NEDGEKEYS + corner * TB + (int)pb;
 }
 
 // Ray bins.  FP64 form: one double per bin, atomic FP64 adds.  FP32 form: the
@@ -567,7 +581,7 @@ __device__ __forceinline__ void deposit_eps_variant(const WalkArgs& a, double* b
     const int nr = a.nr;
     EpsSpread sp;
     eps_setup(a, d, (double)s_edge, sp);
-    const real inv_m3v = real(1.0) / real(TM * TM * TM);
+    const real inv_m3v = real(1.0) / real(TW);
     for (int k = 0; k < ne; ++k) {
         const uint32_t en = __ldg(a.tent + off + k);
         const int b = (int)(en >> 16) * nr + sp.lo;
@@ -613,7 +627,7 @@ __device__ void deposit_eps(const WalkArgs& a, double* bins_eps, uint32_t off, i
             w0 = real(1) - w1;
         }
     }
-    const real inv_m3 = real(1.0) / real(TM * TM * TM);
+    const real inv_m3 = real(1.0) / real(TW);
     for (int k = 0; k < ne; ++k) {
         const uint32_t en = __ldg(a.tent + off + k);
         const int b = (int)(en >> 16) * nr + i;
@@ -649,7 +663,14 @@ __device__ __forceinline__ double alpha_at(const WalkArgs& a, const double* ba, 
 // Far-to-near sweep of one ray (Sec. 2.5) straight from its bins: ba, be, bee
 // are the ray's N_R slots of alpha, eps and e (raw deposits).  Rays without
 // emission cost only the scan for it.  The eps slots are overwritten with the
-// photon rates Phi_j (FP64).
+// photon rates Phi_j (FP64).  All of it is FP64 arithmetic (the FP32 forms'
+// coefficients widened), counted to few FP64 instructions per segment and
+// source: GB300 issues FP64 at 1/64 of the FP32 rate.  The loss of source j
+// over segment i is R_ij = (alpha_i + alpha_{i+1}) G_ij zeta_d zeta_s with
+// G_ij = (1/2) dV_ij zeta_g,ij (Eq. 14-16), and Phi_j <- max(Phi_j - R_ij, 0)
+// (Eq. 13) is one FMA and a test of the sign bit.
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+
 template <int MODE>
 __device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, const double* bee, const Scales& sc) {
     const int nr = a.nr;
@@ -673,13 +694,13 @@ __device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, con
         const uint64_t a0 = (b < 64) ? (m0 & (~0ull << b)) : 0ull;
         const uint64_t a1 = (b <= 64) ? m1 : (m1 & (~0ull << (b - 64)));
         if (a0 | a1) {
-            const double A = 0.5 * (a_lo + a_hi);
+            const double A = a_lo + a_hi;                         // twice the mean coefficient
             const double* g = a.G + (size_t)i * nr;
             if (!bee && __popcll((long long)a0) + __popcll((long long)a1) == 1) {
                 // one source on the segment: zeta_s = 1, and zeta_d = 1 without e
                 const int j = a0 ? __ffsll((long long)a0) - 1 : 64 + __ffsll((long long)a1) - 1;
-                const double np = ph[j] - A * __ldg(g + j);                   // Eq. 13-14
-                if (np > 0.0) ph[j] = np;
+                const double np = fma(-A, __ldg(g + j), ph[j]);   // Eq. 13-14
+                if (positive(np)) ph[j] = np;
                 else { ph[j] = 0.0; if (j < 64) m0 &= ~(1ull << j); else m1 &= ~(1ull << (j - 64)); }
             } else {
                 const double* id2 = a.ID2 + (size_t)i * nr;
@@ -687,23 +708,23 @@ __device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, con
                 double Ftot = 0.0;                                // Eq. 11 at the segment midpoint
                 for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Ftot = fma(ph[j], __ldg(id2 + j), Ftot); }
                 for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Ftot = fma(ph[j], __ldg(id2 + j), Ftot); }
-                if (Ftot > 0.0) {
+                if (positive(Ftot)) {
                     const double inv_F = recip_nr(Ftot);
                     double zd = 1.0;                              // Eq. 17
                     if (bee) {
                         const double ev = alpha_at<MODE>(a, bee, i + 1, ie);
-                        if (ev > 0.0) zd = fmin(2.0, Ftot * recip_nr(ev));
+                        if (positive(ev)) zd = fmin(2.0, Ftot * recip_nr(ev));
                     }
                     const double cf = A * zd * inv_F;             // zeta_s = F_j / Ftot (Eq. 16)
                     for (uint64_t w = a0; w; w &= w - 1) {
                         const int j = __ffsll((long long)w) - 1;
-                        const double np = ph[j] - cf * (__ldg(gi + j) * ph[j]);                  // Eq. 13-14
-                        if (np > 0.0) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
+                        const double np = fma(-cf * __ldg(gi + j), ph[j], ph[j]);   // Eq. 13-14
+                        if (positive(np)) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
                     }
                     for (uint64_t w = a1; w; w &= w - 1) {
                         const int j = 64 + __ffsll((long long)w) - 1;
-                        const double np = ph[j] - cf * (__ldg(gi + j) * ph[j]);
-                        if (np > 0.0) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
+                        const double np = fma(-cf * __ldg(gi + j), ph[j], ph[j]);
+                        if (positive(np)) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
                     }
                 }
             }
@@ -797,7 +818,7 @@ __device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* b
             cnt += __shfl_xor_sync(gmask, cnt, o);
         }
         if (cnt > 0) {
-            const float A = 0.5f * (a_lo + a_hi);
+            const float A = a_lo + a_hi;                      // G carries the 1/2 of the mean
             const bool single = !bee && cnt == 1;             // zeta_s = 1, zeta_d = 1
             float cf = 0.f;
             bool go = true;
@@ -853,7 +874,10 @@ __device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, 
     const int nr = a.nr, tid = threadIdx.x;
     double Fk = 0.0;
     if (MODE != 2) {
-        for (int k = tid; k < a.npix; k += NT)
+        // ray k on warp k % NW: the FP64 work spreads evenly over the SM's
+        // four schedulers (N_PIX = 48 with 4 warps: 12 rays each)
+        constexpr int NW = NT / 32;
+        for (int k = (tid & 31) * NW + (tid >> 5); k < a.npix; k += NT)
             Fk += sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
     } else {
         const int gl = tid % SG, lane = tid & 31;
@@ -923,7 +947,7 @@ template <int MODE>
 __device__ __forceinline__ void deposit_cd(const WalkArgs& a, double* bins, uint32_t off, int ne,
                                            typename Prec<MODE>::real m, typename Prec<MODE>::real d) {
     const double md = (double)m / (a.cd_omega * ((double)d * (double)d));
-    const double inv_m3 = 1.0 / (double)(TM * TM * TM);
+    const double inv_m3 = 1.0 / (double)TW;
     for (int k = 0; k < ne; ++k) {
         const uint32_t en = __ldg(a.tent + off + k);
         atomicAdd(bins + (en >> 16), ((double)(en & 0xffffu) * inv_m3) * md);
@@ -952,7 +976,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const WalkArgs& a = s_a;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    const real inv_m3 = real(1.0) / real(TM * TM * TM);
+    const real inv_m3 = real(1.0) / real(TW);
     const int64_t total = job_end[n_jobs - 1];
     WalkCounters cnt;                                        // per-thread counters
     float kap = 0.f;                                         // FP32 forms: the tree's kappa

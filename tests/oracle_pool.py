@@ -27,6 +27,11 @@ def _worker(args):
         w = workload(spec, **over)
         t = oracle.Tree(w)
         p = oracle.params_for(w)
+    elif kind == "scene":
+        from workloads import scenes
+        w = getattr(scenes, spec["fn"])(**spec.get("kw", {}))
+        t = oracle.Tree(w)
+        p = oracle.params_for(w, **over)
     else:
         from workloads.amr import amr_cluster
         w = amr_cluster(**spec)
@@ -41,8 +46,9 @@ def processes(n_targets: int, per_process: int = 2000) -> int:
 
 def oracle_pass(kind: str, spec, targets, over=None, nproc: int | None = None):
     """F, e, ion of the oracle's single pass at `targets` (cell indices).
-    kind "uniform": spec is a workload name; "amr": spec holds the keyword
-    arguments of workloads.amr.amr_cluster."""
+    kind "uniform": spec is a workload name; "scene": spec = {"fn": a
+    generator of workloads.scenes, "kw": its keyword arguments}; "amr": spec
+    holds the keyword arguments of workloads.amr.amr_cluster."""
     targets = np.asarray(targets, dtype=np.int64)
     over = over or {}
     nproc = nproc or processes(targets.size)
