@@ -252,22 +252,25 @@ def run_walk_only(args):
                       "counters": B.tr_tree_stats(tree), "tree": tree.info(), "ms_per_launch": ms}), flush=True)
 
 
-def l2_copy_peak(devn):
-    """L2 bandwidth ceiling: a plain device copy between two 32 MB buffers
-    that stay resident in the 129 MB L2 (read + write bytes, best of 50)."""
+def l2_copy_peak(devn, mb=16, reps=20):
+    """L2 bandwidth ceiling: a plain device copy between two `mb` MB buffers
+    that stay resident in the 129 MB L2 (read + write bytes), `reps` copies
+    back to back between two events so that launch gaps do not count; best
+    of 10."""
     import torch
-    a = torch.ones(8 << 20, dtype=torch.float32, device=devn)
+    a = torch.ones(mb << 18, dtype=torch.float32, device=devn)
     b = torch.empty_like(a)
     for _ in range(5):
         b.copy_(a)
     best = math.inf
-    for _ in range(50):
+    for _ in range(10):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
-        b.copy_(a)
+        for _ in range(reps):
+            b.copy_(a)
         s1.record()
         torch.cuda.synchronize()
-        best = min(best, s0.elapsed_time(s1))
+        best = min(best, s0.elapsed_time(s1) / reps)
     return 2 * a.numel() * 4 / (best * 1e-3) / 1e9
 
 
@@ -423,7 +426,8 @@ def run_ours(args):
     hbm = {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
            "peak_source": f"{hbm_src} hbm_gbs (MEASURED_PEAKS.json)"}
     l2 = {"achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
-          "peak_source": "measured in this run: device copy between two 32 MB L2-resident buffers"}
+          "peak_source": "measured in this run: device copies between two 16 MB L2-resident buffers, "
+                         "20 back to back per timing"}
     issue = None
     if inst:
         ia = inst / walk_s / 1e9
@@ -454,7 +458,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"independent problem per GPU x{world}"},
         "latency_ms": {"p50": statistics.median(r1["step_ms"]), "p99": percentile(r1["step_ms"], 99),
-                       "note": "over the timed steps; the serving block has the request-latency distribution"},
+                       "note": "over the timed steps; see solve_latency_ms and the serving block for distributions"},
         "forms": {"fp32_sweep64": form_summary(1, r1, args.steps), "fp64": form_summary(0, r0, k_other),
                   "fp32_sweepdf": form_summary(2, r2, max(2, min(args.steps, 5)))},
         "plain_fp64": form_summary(0, r0, k_other),
@@ -465,6 +469,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if world == 1:
+        out["solve_latency_ms"] = solve_latency(B, devn)
     if world == 1 and args.configs != "none":
         names = EXTRA_CONFIGS if args.configs == "all" else tuple(args.configs.split(","))
         out["configs"] = extra_configs(B, names, devn, sha)
@@ -481,6 +487,34 @@ def run_ours(args):
 def percentile(xs, p):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, max(0, int(math.ceil(p / 100.0 * len(xs))) - 1))]
+
+
+def solve_latency(B, devn, name="stromgren32", n=100):
+    """Latency distribution of n end-to-end tr_solve calls (host inputs in
+    pinned memory, host copy of the flux) on a small problem, one after
+    another, FP32 + FP64-sweep form."""
+    import numpy as np
+    import torch
+    from workloads import workload
+    w = workload(name, theta_src=0.25)
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+            for k, v in (("n_H", w.n_H), ("xyz", w.src_xyz), ("Q", w.src_Q))}
+    d = {k: v.to(devn) for k, v in host.items()}
+    F = torch.empty((w.N,) * 3, dtype=torch.float64, device=devn)
+    F_host = torch.empty_like(F, device="cpu").pin_memory()
+    g, s = B.make_grid(d["n_H"], w.dx), B.make_sources(d["xyz"], d["Q"])
+    p = B.tr_params_default(theta_src=w.theta_src, precision=1)
+    ms = []
+    for k in range(n + 5):
+        t0 = time.perf_counter()
+        for key in d:
+            d[key].copy_(host[key], non_blocking=True)
+        B.tr_solve(g, s, p, F)
+        F_host.copy_(F)
+        if k >= 5:
+            ms.append(1e3 * (time.perf_counter() - t0))
+    return {"workload": f"{name} ({w.N}^3, N_PIX={w.npix})", "calls": n, "p50": percentile(ms, 50),
+            "p99": percentile(ms, 99), "max": max(ms), "clock": "host wall clock around each call"}
 
 
 def extra_configs(B, names, devn, sha):

@@ -94,6 +94,7 @@ struct SweepTables {                        // depend on (N_R, eta_R, N_side, N_
     float* Gf = nullptr;                    // FP32 copies of G, ID2, GI
     float* ID2f = nullptr;
     float* GIf = nullptr;
+    double* HT = nullptr;                   // [j][i] (G_{i-1,j} + G_{i,j}) / V_i: lone-source loss per raw deposit
 };
 
 }  // namespace tr

@@ -42,7 +42,8 @@ constexpr size_t OFF_GI = up(OFF_ID2 + sizeof(double) * NR2);
 constexpr size_t OFF_GF = up(OFF_GI + sizeof(double) * NR2);
 constexpr size_t OFF_ID2F = up(OFF_GF + sizeof(float) * NR2);
 constexpr size_t OFF_GIF = up(OFF_ID2F + sizeof(float) * NR2);
-constexpr size_t OFF_TCOUNTS = up(OFF_GIF + sizeof(float) * NR2);
+constexpr size_t OFF_HT = up(OFF_GIF + sizeof(float) * NR2);
+constexpr size_t OFF_TCOUNTS = up(OFF_HT + sizeof(double) * NR2);
 constexpr size_t OFF_TOFF = up(OFF_TCOUNTS + sizeof(uint32_t) * NKEYS);
 constexpr size_t OFF_THDR = up(OFF_TOFF + sizeof(uint32_t) * (NKEYS + 1));
 constexpr size_t OFF_TENT = up(OFF_THDR + sizeof(uint2) * NKEYS);
@@ -122,6 +123,7 @@ extern "C" tr_status tr_solve_noalloc(const tr_grid* g, const tr_sources* s, con
         ds.sw.Gf = at<float>(ds.base, OFF_GF);
         ds.sw.ID2f = at<float>(ds.base, OFF_ID2F);
         ds.sw.GIf = at<float>(ds.base, OFF_GIF);
+        ds.sw.HT = at<double>(ds.base, OFF_HT);
         ds.ready = true;
     }
     if (!ds.table_ok || ds.table.nside != p->nside) {

@@ -316,10 +316,23 @@ __global__ void k_export(const void* nodes_v, int64_t n, double* out, double U, 
 // source point j > i the loss geometry (1/2) dV_ij zeta_g,ij (Eq. 14-16: the
 // 1/2 of the segment's mean coefficient, so that a sweep multiplies it by
 // alpha_i + alpha_{i+1}) and the inverse square distance from j to the
-// segment midpoint.
+// segment midpoint.  HT[j][i] = (G_{i-1,j} + G_{i,j}) / V_i: the weight of
+// point i's raw recombination deposit in the total loss of a lone source at
+// j (Eq. 13-14 with zeta_s = zeta_d = 1, the volume V_i of the ray cell
+// folded in), so that the total is sum_i bin_i HT[j][i].
+__device__ __forceinline__ double seg_geom(int i, int j, int nr, int eta, int nside, int zeta_g) {
+    if (!(j > i && i + 1 < nr && i >= 0)) return 0.0;
+    auto rad = [eta](int k) { return (double)((int64_t)k * k) / (2.0 * (double)eta * (double)eta); };
+    const double ri = rad(i), ri1 = rad(i + 1), rj = rad(j);
+    const double a = rj - ri, b = rj - ri1;
+    const double dV = (a * a * a - b * b * b) / 3.0;
+    const double zg = zeta_g ? fmin(1.0, (double)nside * (rj - ri) / (2.0 * rj)) : 1.0;
+    return 0.5 * dV * zg;
+}
+
 __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g, double* r, float* rf,
                                double* inv_r2, double* inv_vol, float* inv_volf, double* G, double* ID2, double* GI,
-                               float* Gf, float* ID2f, float* GIf) {
+                               float* Gf, float* ID2f, float* GIf, double* HT) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     auto rad = [eta](int i) { return (double)((int64_t)i * i) / (2.0 * (double)eta * (double)eta); };
     if (t < nr) {
@@ -335,14 +348,10 @@ __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g,
     }
     if (t < nr * nr) {
         const int i = t / nr, j = t % nr;
-        double g = 0.0, id2 = 0.0;
+        const double g = seg_geom(i, j, nr, eta, nside, zeta_g);
+        double id2 = 0.0;
         if (j > i && i + 1 < nr) {
-            const double ri = rad(i), ri1 = rad(i + 1), rj = rad(j);
-            const double a = rj - ri, b = rj - ri1;
-            const double dV = (a * a * a - b * b * b) / 3.0;
-            const double zg = zeta_g ? fmin(1.0, (double)nside * (rj - ri) / (2.0 * rj)) : 1.0;
-            g = 0.5 * dV * zg;
-            const double rm = 0.5 * (ri + ri1);
+            const double rm = 0.5 * (rad(i) + rad(i + 1)), rj = rad(j);
             id2 = 1.0 / ((rj - rm) * (rj - rm));
         }
         G[t] = g;
@@ -351,6 +360,11 @@ __global__ void k_sweep_tables(int nr, int eta, int nside, int npix, int zeta_g,
         Gf[t] = (float)g;
         ID2f[t] = (float)id2;
         GIf[t] = (float)(g * id2);
+        const int jj = t / nr, ii = t % nr;                 // HT is indexed [j][i]
+        const double lo = (ii == 0) ? 0.0 : 0.5 * (rad(ii - 1) + rad(ii));
+        const double hi = (ii == nr - 1) ? rad(ii) : 0.5 * (rad(ii) + rad(ii + 1));
+        const double vol = (4.0 * PI_D / (double)npix) * (hi * hi * hi - lo * lo * lo) / 3.0;
+        HT[t] = (seg_geom(ii - 1, jj, nr, eta, nside, zeta_g) + seg_geom(ii, jj, nr, eta, nside, zeta_g)) / vol;
     }
 }
 
@@ -379,14 +393,15 @@ tr_status sweep_tables_make(SweepTables* sw, int nr, int eta, int nside, int npi
         cudaMalloc(&sw->GI, sizeof(double) * n2) != cudaSuccess ||
         cudaMalloc(&sw->Gf, sizeof(float) * n2) != cudaSuccess ||
         cudaMalloc(&sw->ID2f, sizeof(float) * n2) != cudaSuccess ||
-        cudaMalloc(&sw->GIf, sizeof(float) * n2) != cudaSuccess) {
+        cudaMalloc(&sw->GIf, sizeof(float) * n2) != cudaSuccess ||
+        cudaMalloc(&sw->HT, sizeof(double) * n2) != cudaSuccess) {
         cudaGetLastError();
         sweep_tables_free(sw);
         return set_error(TR_ENOMEM, "cannot allocate the ray tables (N_R = %d)", nr);
     }
     k_sweep_tables<<<grid_for((int64_t)n2, 128), 128, 0, st>>>(nr, eta, nside, npix, zeta_g, sw->r, sw->rf,
                                                                 sw->inv_r2, sw->inv_vol, sw->inv_volf, sw->G, sw->ID2, sw->GI,
-                                                                sw->Gf, sw->ID2f, sw->GIf);
+                                                                sw->Gf, sw->ID2f, sw->GIf, sw->HT);
     s = cuda_check(cudaGetLastError(), "ray table kernel");
     if (s != TR_OK) return s;
     sw->nr = nr; sw->eta = eta; sw->nside = nside; sw->zeta_g = zeta_g;
@@ -397,7 +412,7 @@ tr_status sweep_tables_fill(SweepTables* sw, int nr, int eta, int nside, int npi
     const size_t n2 = (size_t)nr * nr;
     k_sweep_tables<<<grid_for((int64_t)n2, 128), 128, 0, st>>>(nr, eta, nside, npix, zeta_g, sw->r, sw->rf,
                                                                 sw->inv_r2, sw->inv_vol, sw->inv_volf, sw->G, sw->ID2,
-                                                                sw->GI, sw->Gf, sw->ID2f, sw->GIf);
+                                                                sw->GI, sw->Gf, sw->ID2f, sw->GIf, sw->HT);
     tr_status s = cuda_check(cudaGetLastError(), "ray table kernel");
     if (s != TR_OK) return s;
     sw->nr = nr; sw->eta = eta; sw->nside = nside; sw->zeta_g = zeta_g;
@@ -407,6 +422,7 @@ tr_status sweep_tables_fill(SweepTables* sw, int nr, int eta, int nside, int npi
 void sweep_tables_free(SweepTables* sw) {
     cudaFree(sw->r); cudaFree(sw->rf); cudaFree(sw->inv_r2); cudaFree(sw->inv_vol); cudaFree(sw->inv_volf);
     cudaFree(sw->G); cudaFree(sw->ID2); cudaFree(sw->GI); cudaFree(sw->Gf); cudaFree(sw->ID2f); cudaFree(sw->GIf);
+    cudaFree(sw->HT);
     *sw = SweepTables();
 }
 

@@ -72,6 +72,7 @@ struct WalkArgs {
     const float* Gf;
     const float* ID2f;
     const float* GIf;
+    const double* HT;                       // [j][i] lone-source loss per raw recombination deposit
     const int64_t* targets;                 // NULL: cells first .. first+n_targets-1 in walk order
     int64_t first;
     const uint8_t* flags;                   // AMR tree: node topology (NULL: uniform grid)
@@ -687,6 +688,22 @@ __device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, con
     double* ph = be;                                              // Eq. 12
     const float ia = 1.0f / sc.a, ie = 1.0f / sc.e;
     const int jtop = m1 ? 64 + 63 - __clzll((long long)m1) : 63 - __clzll((long long)m0);
+    if (!bee && __popcll((long long)m0) + __popcll((long long)m1) == 1) {
+        // a lone source and no e: zeta_s = zeta_d = 1 on every segment, every
+        // R_ij >= 0, so clipping once at the end equals clipping per segment
+        // (Eq. 13): Phi_0 = max(Phi_j - sum_i bin_i HT[j][i], 0), an FP64 dot
+        // product (two accumulators to halve the dependency chain)
+        const double* h = a.HT + (size_t)jtop * nr;
+        double s0 = 0.0, s1 = 0.0;
+        int i = 0;
+        for (; i + 1 <= jtop; i += 2) {
+            s0 = fma((double)(MODE == 0 ? ba[i] : (double)bin_value_f<MODE>(ba + i, ia)), __ldg(h + i), s0);
+            s1 = fma((double)(MODE == 0 ? ba[i + 1] : (double)bin_value_f<MODE>(ba + i + 1, ia)), __ldg(h + i + 1), s1);
+        }
+        if (i <= jtop) s0 = fma((double)(MODE == 0 ? ba[i] : (double)bin_value_f<MODE>(ba + i, ia)), __ldg(h + i), s0);
+        const double phi = ph[jtop] - (s0 + s1);
+        return positive(phi) ? phi * __ldg(a.inv_r2 + jtop) : 0.0;
+    }
     double a_hi = alpha_at<MODE>(a, ba, jtop, ia);
     for (int i = jtop - 1; i >= 0 && (m0 | m1); --i) {
         const double a_lo = alpha_at<MODE>(a, ba, i, ia);
@@ -874,10 +891,10 @@ __device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, 
     const int nr = a.nr, tid = threadIdx.x;
     double Fk = 0.0;
     if (MODE != 2) {
-        // ray k on warp k % NW: the FP64 work spreads evenly over the SM's
-        // four schedulers (N_PIX = 48 with 4 warps: 12 rays each)
-        constexpr int NW = NT / 32;
-        for (int k = (tid & 31) * NW + (tid >> 5); k < a.npix; k += NT)
+        // consecutive rays on consecutive lanes: GB300 charges an FP64 warp
+        // instruction in full however few lanes it has, so the FP64 work is
+        // packed into as few warps as there are rays / 32
+        for (int k = tid; k < a.npix; k += NT)
             Fk += sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
     } else {
         const int gl = tid % SG, lane = tid & 31;
@@ -1445,6 +1462,7 @@ WalkArgs make_args(const tr_tree* t) {
     a.toff = t->table->off; a.tent = t->table->ent; a.hdr = t->table->hdr;
     a.r = t->sw.r; a.rf = t->sw.rf; a.inv_r2 = t->sw.inv_r2; a.inv_vol = t->sw.inv_vol; a.inv_volf = t->sw.inv_volf;
     a.G = t->sw.G; a.ID2 = t->sw.ID2; a.GI = t->sw.GI; a.Gf = t->sw.Gf; a.ID2f = t->sw.ID2f; a.GIf = t->sw.GIf;
+    a.HT = t->sw.HT;
     a.Fconv = t->U / (t->dx * t->dx);
     a.Econv = t->Eu;
     a.status = t->status;
@@ -1654,6 +1672,7 @@ tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaSt
     WalkArgs a{};
     a.nr = r->nr; a.npix = r->npix; a.use_e = r->use_e;
     a.r = r->sw.r; a.inv_r2 = r->sw.inv_r2; a.inv_vol = r->sw.inv_vol; a.inv_volf = r->sw.inv_volf; a.G = r->sw.G; a.ID2 = r->sw.ID2; a.GI = r->sw.GI; a.Gf = r->sw.Gf; a.ID2f = r->sw.ID2f; a.GIf = r->sw.GIf;
+    a.HT = r->sw.HT;
     a.n_targets = r->n_targets;
     a.Fconv = r->U / (r->dx * r->dx);
     a.Econv = r->Eu;

@@ -8,10 +8,12 @@ over time.  The loop
   fit yet);
 * builds an admitted request's tree once and keeps it resident until the
   request is done;
-* every tick, launches ONE persistent walk kernel (tr_walk_sweep_batch) over
+* launches ONE persistent walk kernel (tr_walk_sweep_batch) at a time over
   a slice of the remaining target cells of every active request: requests
   with the least remaining work get their slice first, large requests are cut
-  into Morton ranges so that they do not hold up small ones;
+  into Morton ranges so that they do not hold up small ones; while it runs,
+  new arrivals are admitted, uploaded and built on a second stream, and
+  finished results copied back;
 * retires a request when its last slice is done and records its latency
   (completion - arrival).
 
@@ -42,6 +44,7 @@ class Request:
     make: object = None                 # optional: fills n_H, src_xyz, src_Q when called (lazy request data)
     # filled by the server
     admitted: float | None = None
+    footprint: int = 0                  # device bytes counted against the budget while resident
     done: float | None = None
     next_target: int = 0
     result: dict | None = None
@@ -59,14 +62,27 @@ class Request:
         return None if self.done is None else self.done - self.arrival
 
 
-def footprint_bytes(N: int, precision: int) -> int:
-    """Device bytes a request holds while resident: its tree (node records and
-    build sums), mapped emission, inputs and outputs."""
+def num_points(N: int, eta_r: int = 2) -> int:
+    """N_R of a uniform N^3 grid with the default L_ray (the box diagonal, Eq. 5)."""
+    return eta_r * int(math.floor(math.sqrt(2.0 * N * math.sqrt(3.0)))) + 1
+
+
+def footprint_bytes(N: int, precision: int, n_sources: int = 1000, eta_r: int = 2) -> int:
+    """Device bytes a request holds while resident: its tree (node records
+    and build sums; the FP32 forms keep the FP64 tree beside the FP32 one),
+    mapped emission, ray tables, inputs and outputs, each allocation rounded
+    up to 2 MiB (the device allocator's granularity for large blocks).  The
+    node->ray table of each N_side is shared by all requests and is not
+    counted here."""
+    def rounded(b):
+        return -(-int(b) // (2 << 20)) * (2 << 20)
     n_nodes = ((1 << (3 * (int(math.log2(N)) + 1))) - 1) // 7
-    rec = 64 if precision == 0 else 32
-    sums = 24 if precision == 0 else 12
     cells = N ** 3
-    return n_nodes * (rec + sums) + cells * (8 + 8 + 8 + 8 + 1) + 4096
+    nr = num_points(N, eta_r)
+    tree = [n_nodes * 64, n_nodes * 24] if precision == 0 else [n_nodes * 32, n_nodes * 12, n_nodes * 64, n_nodes * 24]
+    tree += [cells * 8, 7 * nr * nr * 8 + 5 * nr * 8, 4096]                # emission, ray tables, small state
+    io = [cells * 8, n_sources * 32, cells * 8, cells * 8, cells]           # n_H, sources, F, e, ion
+    return sum(rounded(b) for b in tree + io)
 
 
 class Scheduler:
@@ -88,7 +104,8 @@ class Scheduler:
     def admit(self, now: float) -> list[Request]:
         admitted = []
         for req in list(self.waiting):
-            fp = footprint_bytes(req.N, self.precision)
+            fp = footprint_bytes(req.N, self.precision, len(req.src_Q) if req.src_Q is not None else 1000)
+            req.footprint = fp
             if fp > self.budget:
                 raise ValueError(f"request {req.rid} needs {fp} bytes, more than the whole budget {self.budget}")
             if self.in_use + fp <= self.budget:
@@ -121,7 +138,7 @@ class Scheduler:
             if req.remaining == 0:
                 req.done = now
                 self.active.remove(req)
-                self.in_use -= footprint_bytes(req.N, self.precision)
+                self.in_use -= req.footprint
                 self.finished.append(req)
                 done.append(req)
         return done
@@ -133,12 +150,21 @@ class Scheduler:
 class Server:
     """Scheduler plus the device work (tree builds and batched walks).
 
+    The batched walk runs on a stream of its own, launched from a worker
+    thread (the C call releases the interpreter lock and returns when its
+    launch is done), so that while one batch is on the GPU the host keeps
+    admitting arrivals, uploads their inputs and builds their trees on a
+    side stream, and copies finished results back to pinned host memory.
+    The next batch waits on the builds of the trees it walks (CUDA events),
+    not on the host.
+
     keep_results=False returns each result to the host and keeps only a
     summary (the flux total), for long streams whose results would not fit
     in host memory together."""
 
     def __init__(self, budget_bytes: int, tick_targets: int = 1 << 20, precision: int = 1, device=None,
                  keep_results: bool = True):
+        import concurrent.futures
         import torch
         from . import binding as B
         self.B = B
@@ -150,6 +176,11 @@ class Server:
         self.t0 = time.perf_counter()
         self.launches = 0
         self.keep_results = keep_results
+        self.side = None                                        # uploads, builds, result copies
+        self.walk = None                                        # batched walks (both made on first use)
+        self.worker = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+        self.inflight = None                                    # (future, slices) of the running batch
+        self.copies = []                                        # results on their way to the host
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -157,41 +188,89 @@ class Server:
     def submit(self, req: Request):
         self.sched.submit(req)
 
+    def _streams(self):
+        if self.side is None:
+            self.side = self.torch.cuda.Stream(device=self.dev)
+            self.walk = self.torch.cuda.Stream(device=self.dev)
+
     def _start(self, req: Request):
+        """Upload the request and build its tree on the side stream (no wait)."""
         torch, B = self.torch, self.B
-        d = dict(n_H=torch.from_numpy(np.ascontiguousarray(req.n_H)).to(self.dev),
-                 xyz=torch.from_numpy(np.ascontiguousarray(req.src_xyz)).to(self.dev),
-                 Q=torch.from_numpy(np.ascontiguousarray(req.src_Q)).to(self.dev))
-        shape = (req.N,) * 3
-        d["F"] = torch.empty(shape, dtype=torch.float64, device=self.dev)
-        d["e"] = torch.empty_like(d["F"])
-        d["ion"] = torch.empty(shape, dtype=torch.uint8, device=self.dev)
-        p = B.tr_params_default(nside=req.nside, theta_lim=req.theta_lim, theta_src=req.theta_src,
-                                precision=self.precision)
-        d["tree"] = B.tr_build_tree(B.make_grid(d["n_H"], req.dx), B.make_sources(d["xyz"], d["Q"]), p)
+        self._streams()
+        with torch.cuda.stream(self.side):
+            d = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().to(self.dev, non_blocking=True)
+                 for k, a in (("n_H", req.n_H), ("xyz", req.src_xyz), ("Q", req.src_Q))}
+            shape = (req.N,) * 3
+            d["F"] = torch.empty(shape, dtype=torch.float64, device=self.dev)
+            d["e"] = torch.empty_like(d["F"])
+            d["ion"] = torch.empty(shape, dtype=torch.uint8, device=self.dev)
+            p = B.tr_params_default(nside=req.nside, theta_lim=req.theta_lim, theta_src=req.theta_src,
+                                    precision=self.precision)
+            d["tree"] = B.tr_build_tree(B.make_grid(d["n_H"], req.dx), B.make_sources(d["xyz"], d["Q"]), p,
+                                        stream=self.side)
+            d["ready"] = torch.cuda.Event()
+            d["ready"].record(self.side)
         self.state[req.rid] = d
         if req.make is not None:                 # the host copy of lazy request data is no longer needed
             req.n_H = None
 
-    def _finish(self, req: Request):
-        d = self.state.pop(req.rid)
-        res = dict(F=d["F"].cpu().numpy(), e=d["e"].cpu().numpy(), ion=d["ion"].cpu().numpy())
-        req.result = res if self.keep_results else dict(F_sum=float(res["F"].sum()), ionised=int(res["ion"].sum()))
-
-    def tick(self) -> int:
-        """Admit, launch one batch, retire; returns the number of targets done."""
-        for req in self.sched.admit(self.now()):
-            self._start(req)
-        slices = self.sched.plan()
-        if not slices:
-            return 0
+    def _launch(self, slices):
+        self._streams()
         st = [self.state[r.rid] for r, _, _ in slices]
-        self.B.tr_walk_sweep_batch([d["tree"] for d in st], [f for _, f, _ in slices], [c for _, _, c in slices],
-                                   [d["F"] for d in st], [d["e"] for d in st], [d["ion"] for d in st])
+        for d in st:
+            self.walk.wait_event(d["ready"])
+        fut = self.worker.submit(self.B.tr_walk_sweep_batch, [d["tree"] for d in st], [f for _, f, _ in slices],
+                                 [c for _, _, c in slices], [d["F"] for d in st], [d["e"] for d in st],
+                                 [d["ion"] for d in st], self.walk)
+        self.inflight = (fut, slices)
+
+    def _retire(self):
+        fut, slices = self.inflight
+        fut.result()                             # raises what the batch raised
+        self.inflight = None
         self.launches += 1
         for req in self.sched.complete(slices, self.now()):
             self._finish(req)
-        return sum(c for _, _, c in slices)
+
+    def _finish(self, req: Request):
+        """Copy a finished request's results to pinned host memory (side stream)."""
+        torch = self.torch
+        d = self.state.pop(req.rid)
+        with torch.cuda.stream(self.side):
+            host = {k: torch.empty(d[k].shape, dtype=d[k].dtype, pin_memory=True) for k in ("F", "e", "ion")}
+            for k in host:
+                host[k].copy_(d[k], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.side)
+        self.copies.append((req, ev, host, d))
+
+    def _drain(self, block: bool = False):
+        left = []
+        for req, ev, host, d in self.copies:
+            if block:
+                ev.synchronize()
+            if not ev.query():
+                left.append((req, ev, host, d))
+                continue
+            res = {k: v.numpy() for k, v in host.items()}
+            req.result = res if self.keep_results else dict(F_sum=float(res["F"].sum()), ionised=int(res["ion"].sum()))
+        self.copies = left
+
+    def tick(self) -> int:
+        """One scheduling round: admit and start builds, retire the running
+        batch if it is done, launch the next; returns targets launched."""
+        for req in self.sched.admit(self.now()):
+            self._start(req)
+        if self.inflight is not None and self.inflight[0].done():
+            self._retire()
+        launched = 0
+        if self.inflight is None:
+            slices = self.sched.plan()
+            if slices:
+                self._launch(slices)
+                launched = sum(c for _, _, c in slices)
+        self._drain()
+        return launched
 
     def run(self, requests: list[Request], prefetch: int = 4) -> list[Request]:
         """Replay requests at their arrival times (seconds after start).
@@ -213,18 +292,25 @@ class Server:
         filler.start()
         self.t0 = time.perf_counter()
         i = 0
-        while i < len(pending) or not self.sched.idle():
-            now = self.now()
-            while i < len(pending) and pending[i].arrival <= now and ready[i].is_set():
-                self.submit(pending[i])
-                i += 1
-            started = [r for r in self.sched.waiting]
-            if self.tick() == 0 and i < len(pending):
-                time.sleep(max(0.0, min(0.002, pending[i].arrival - self.now())))
-            for r in started:
-                if r.make is not None and r.admitted is not None and r.n_H is None:
-                    slots.release()
-        filler.join()
+        try:
+            while i < len(pending) or not self.sched.idle() or self.inflight is not None:
+                now = self.now()
+                while i < len(pending) and pending[i].arrival <= now and ready[i].is_set():
+                    self.submit(pending[i])
+                    i += 1
+                started = [r for r in self.sched.waiting]
+                if self.tick() == 0:
+                    time.sleep(0.0005 if self.inflight is not None else
+                               max(0.0, min(0.002, pending[i].arrival - self.now())) if i < len(pending) else 0.0005)
+                for r in started:
+                    if r.make is not None and r.admitted is not None and r.n_H is None:
+                        slots.release()
+        finally:
+            if self.inflight is not None:
+                self.inflight[0].result()
+                self.inflight = None
+            self._drain(block=True)
+            filler.join()
         return self.sched.finished
 
 

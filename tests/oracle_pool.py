@@ -18,7 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _worker(args):
-    kind, spec, over, targets = args
+    kind, spec, over, targets = args[:4]
+    free = len(args) > 4 and args[4]
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
     import oracle
@@ -37,6 +38,8 @@ def _worker(args):
         w = amr_cluster(**spec)
         t = oracle.AmrTree(w)
         p = oracle.params_for(w, **over)
+    if free:
+        return t.free_flux(p, targets=np.asarray(targets, dtype=np.int64))
     return t.solve_pass(p, targets=np.asarray(targets, dtype=np.int64))
 
 
@@ -58,6 +61,19 @@ def oracle_pass(kind: str, spec, targets, over=None, nproc: int | None = None):
     with mp.get_context("spawn").Pool(len(chunks)) as pool:
         parts = pool.map(_worker, [(kind, spec, over, c) for c in chunks])
     return tuple(np.concatenate([p[k] for p in parts]) for k in range(3))
+
+
+def oracle_free(kind: str, spec, targets, over=None, nproc: int | None = None):
+    """The oracle's unattenuated flux at `targets` (see oracle_pass)."""
+    targets = np.asarray(targets, dtype=np.int64)
+    over = over or {}
+    nproc = nproc or processes(targets.size)
+    if nproc == 1 or targets.size < 64:
+        return _worker((kind, spec, over, targets, True))
+    chunks = [c for c in np.array_split(targets, nproc) if c.size]
+    with mp.get_context("spawn").Pool(len(chunks)) as pool:
+        parts = pool.map(_worker, [(kind, spec, over, c, True) for c in chunks])
+    return np.concatenate(parts)
 
 
 def uniform_neighbours(targets, N: int):
@@ -107,14 +123,16 @@ def amr_neighbours(g, targets):
     return out
 
 
-def sampled_check(F, ion, targets, nbrs, oracle_fn, rtol):
+def sampled_check(F, ion, targets, nbrs, oracle_fn, rtol, kappa=0.0, free_fn=None):
     """Compare the GPU field at sampled targets with the oracle, cell by
     cell.  A sampled cell is at the front when the oracle puts one of its
     face neighbours in the other class; every other sampled cell must have
-    the oracle's class and, if lit, its flux within rtol, or exactly zero
-    flux if dark.  No fraction of the sample is exempt.  oracle_fn(cells)
-    returns the oracle's (F, e, ion) at those cells.  Returns the number of
-    interior cells checked and the largest relative error."""
+    the oracle's class and, if lit, its flux within rtol (FP32 forms: within
+    rtol F + kappa (F_free - F) where the plain bar is missed, free_fn(cells)
+    giving the oracle's unattenuated flux), or exactly zero flux if dark.
+    No fraction of the sample is exempt.  oracle_fn(cells) returns the
+    oracle's (F, e, ion) at those cells.  Returns the number of interior
+    cells checked and the largest relative error."""
     targets = np.asarray(targets, dtype=np.int64)
     allc = np.unique(np.concatenate([targets] + [np.asarray(n, dtype=np.int64) for n in nbrs]))
     allc = allc[allc >= 0]
@@ -138,5 +156,12 @@ def sampled_check(F, ion, targets, nbrs, oracle_fn, rtol):
                 bad.append((int(t), "flux", float(F[t]), float(Fo[k])))
         elif F[t] != 0.0:
             bad.append((int(t), "dark", float(F[t]), 0.0))
+    flux_bad = [b for b in bad if b[1] == "flux"]
+    if flux_bad and kappa > 0.0 and free_fn is not None:
+        cells = np.array([b[0] for b in flux_bad], dtype=np.int64)
+        Ff = np.asarray(free_fn(cells))
+        keep = {int(c) for c, f, b in zip(cells, Ff, flux_bad)
+                if abs(b[2] - b[3]) > rtol * b[3] + kappa * (f - b[3])}
+        bad = [b for b in bad if b[1] != "flux" or b[0] in keep]
     assert not bad, f"{len(bad)} of {checked} interior sampled cells miss the bar: {bad[:5]}"
     return checked, worst

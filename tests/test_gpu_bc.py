@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from test_gpu_amr import compare_amr, gpu_amr_solve, small_amr
+from helpers import KAPPA
 from test_gpu_parity import B, RTOL, compare_fields, dev, gpu_solve, gpu_tree, small_turbulent  # noqa: F401
 
 pytestmark = pytest.mark.gpu
@@ -46,8 +47,10 @@ def test_bc_walk_lists_and_bins_fp64(B, orc, bc):
 def test_bc_solve(B, orc, bc, precision):
     w = small_turbulent(N=32, theta_src=0.4)
     F, e, ion = gpu_solve(B, w, precision, bc=bc)
-    F_orc, _, ion_orc = orc.Tree(w).solve_pass(orc.params_for(w, bc=bc))
-    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision])
+    ot, p = orc.Tree(w), orc.params_for(w, bc=bc)
+    F_orc, _, ion_orc = ot.solve_pass(p)
+    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision], KAPPA[precision],
+                   lambda c: ot.free_flux(p, targets=c))
 
 
 @pytest.mark.parametrize("bc", BCS)

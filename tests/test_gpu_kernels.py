@@ -6,6 +6,7 @@ the ionisation front."""
 import numpy as np
 import pytest
 
+from helpers import KAPPA
 from test_gpu_parity import B, RTOL, compare_fields, dev, gpu_solve, gpu_tree, small_turbulent  # noqa: F401
 
 pytestmark = pytest.mark.gpu
@@ -47,8 +48,10 @@ def test_kernel_solve(B, orc, precision, kernel_alpha, kernel_eps):
     w = small_turbulent(N=32, theta_src=0.6)
     kw = dict(kernel_alpha=kernel_alpha, kernel_eps=kernel_eps)
     F, e, ion = gpu_solve(B, w, precision, **kw)
-    F_orc, _, ion_orc = orc.Tree(w).solve_pass(orc.params_for(w, **kw))
-    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision])
+    ot, p = orc.Tree(w), orc.params_for(w, **kw)
+    F_orc, _, ion_orc = ot.solve_pass(p)
+    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision], KAPPA[precision],
+                   lambda c: ot.free_flux(p, targets=c))
 
 
 def test_kernel_choice_is_checked(B):

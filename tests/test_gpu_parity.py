@@ -13,8 +13,8 @@ import math
 import numpy as np
 import pytest
 
-from helpers import interior_mask
-from oracle_pool import oracle_pass, sampled_check, uniform_neighbours
+from helpers import KAPPA, flux_misses, interior_mask
+from oracle_pool import oracle_free, oracle_pass, sampled_check, uniform_neighbours
 from workloads import Workload, PC_CM, lognormal_density, uniform_density, uniform_sources, workload
 
 pytestmark = pytest.mark.gpu
@@ -83,14 +83,21 @@ def gpu_params_dict(w, precision=0, zeta_g=True, **kw):
     return d
 
 
-def compare_fields(F, ion, F_orc, ion_orc, N, rtol):
+def compare_fields(F, ion, F_orc, ion_orc, N, rtol, kappa=0.0, free_fn=None):
+    """Every cell away from the oracle's front: the oracle's class, the flux
+    within rtol (FP32 forms: within the conditioning bound where the plain
+    bar is missed; free_fn(cell indices) gives the oracle's unattenuated
+    flux), exactly zero where the oracle's is."""
     inner = interior_mask(ion_orc.reshape(N, N, N)).ravel()
     bad = np.nonzero(ion[inner] != ion_orc[inner])[0]
     assert bad.size == 0, f"{bad.size} cells away from the front change class"
-    lit = inner & (F_orc > 0)
-    if lit.any():
+    lit = np.nonzero(inner & (F_orc > 0))[0]
+    if lit.size:
         err = np.abs(F[lit] - F_orc[lit]) / F_orc[lit]
-        assert err.max() <= rtol, f"max rel flux error {err.max():.3e} > {rtol} (median {np.median(err):.2e})"
+        miss = flux_misses(F[lit], F_orc[lit], rtol, kappa, None if free_fn is None else (lambda k: free_fn(lit[k])))
+        worst = lit[np.argsort(-err)[:3]]
+        assert miss.size == 0, (f"{miss.size} cells miss the flux bar; max rel error {err.max():.3e} > {rtol} "
+                                f"(median {np.median(err):.2e}), worst cells {worst.tolist()}")
     dark = inner & (F_orc == 0)
     assert np.all(F[dark] == 0.0)
     # cells that differ in class lie within one cell of the oracle's front
@@ -219,8 +226,10 @@ def test_fp32_lists_with_if_mac(B, orc):
 def test_solve_matches_oracle(B, orc, name, precision):
     w = workload(name, theta_src=0.25) if name == "stromgren32" else workload(name)
     F, e, ion = gpu_solve(B, w, precision)
-    F_orc, e_orc, ion_orc = orc.Tree(w).solve_pass(orc.params_for(w))
-    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision])
+    ot, p = orc.Tree(w), orc.params_for(w)
+    F_orc, e_orc, ion_orc = ot.solve_pass(p)
+    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision], KAPPA[precision],
+                   lambda c: ot.free_flux(p, targets=c))
     np.testing.assert_allclose(e, F * w.hnu / 2.99792458e10, rtol=1e-14)
 
 
@@ -292,10 +301,13 @@ def test_edge_cases(B, orc, case):
         w.ndot_cell = 1e45 * (w.n_H / w.n_H.mean()) ** 2
     zg = kw.get("zeta_g", True)
     lray_cells = pkw.get("L_ray_cm", 0.0) / w.dx
-    F_orc, _, ion_orc = orc.Tree(w, e_prev=e_prev).solve_pass(orc.params_for(w, zeta_g=zg, lray_cells=lray_cells))
+    ot = orc.Tree(w, e_prev=e_prev)
+    p = orc.params_for(w, zeta_g=zg, lray_cells=lray_cells)
+    F_orc, _, ion_orc = ot.solve_pass(p)
     for precision in FORMS:
         F, e, ion = gpu_solve(B, w, precision, e_prev=e_prev, zeta_g=zg, **pkw)
-        compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision])
+        compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision], KAPPA[precision],
+                       lambda c: ot.free_flux(p, targets=c))
 
 
 def test_errors_are_reported(B):
@@ -332,7 +344,8 @@ def test_full_size_turbulent128_every_cell(B, precision):
     w = workload("turbulent128")
     F, e, ion = gpu_solve(B, w, precision)
     F_orc, ion_orc = oracle_full_field("turbulent128")
-    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision])
+    compare_fields(F, ion, F_orc, ion_orc, w.N, RTOL[precision], KAPPA[precision],
+                   lambda c: oracle_free("uniform", "turbulent128", c))
 
 
 @pytest.mark.slow
@@ -348,7 +361,7 @@ def test_full_size_sourcecount256_sampled(B, name, precision):
     targets = rng.choice(w.N ** 3, 60, replace=False).astype(np.int64)
     nb = uniform_neighbours(targets, w.N)
     checked, worst = sampled_check(F, ion, targets, nb, lambda c: oracle_pass("uniform", name, c, nproc=8),
-                                   RTOL[precision])
+                                   RTOL[precision], KAPPA[precision], lambda c: oracle_free("uniform", name, c, nproc=8))
     assert checked >= 30
 
 

@@ -9,20 +9,35 @@ penetration depth equals the oracle's to within one cell.
 Two sources and an opaque cloud (Sec. 3.4): a 64^3 grid, N_PIX = 48,
 theta_lim = 0.5.  One pass on the mid plane against the oracle, and the
 field -- one pass and iterated to convergence (Sec. 2.6) -- symmetric about
-x = y: to rounding in FP64 (FP64 atomic deposits in any order) and to FP32
-rounding of the moments in the FP32 forms.
+x = y: to rounding in FP64 (FP64 atomic deposits in any order) on every lit
+cell; in the FP32 forms, whose mirrored nodes sum their FP32 moments in
+different orders, to twice their parity bar on the cells away from the
+front (each side is within the bar of the oracle, which is symmetric to
+rounding), and the classification there.
 """
 import numpy as np
 import pytest
 
-from oracle_pool import oracle_pass, sampled_check, uniform_neighbours
+from helpers import KAPPA, interior_mask
+from oracle_pool import oracle_free, oracle_pass, sampled_check, uniform_neighbours
 from test_gpu_parity import B, RTOL, dev, gpu_solve  # noqa: F401
 from workloads.scenes import channel_cells, mirror_xy, rabbit_hole, two_sources_cloud
 
 pytestmark = pytest.mark.gpu
 
 FORMS = [0, 1, 2]
-SYM = {0: 1e-10, 1: 1e-4, 2: 1e-4}          # relative x = y asymmetry allowed per form
+SYM = {0: 1e-10, 1: 2e-3, 2: 2e-3}          # relative x = y asymmetry allowed per form
+
+
+def assert_mirror_symmetric(F, ion, precision, scale=1.0):
+    if precision == 0:
+        assert np.array_equal(ion, mirror_xy(ion))
+        check = F > 0
+    else:                                   # FP32 rounding may tip a cell at the front
+        inner = interior_mask(ion) & mirror_xy(interior_mask(ion))
+        assert np.array_equal(ion[inner], mirror_xy(ion)[inner])
+        check = inner & (F > 0)
+    assert np.all(np.abs(F - mirror_xy(F))[check] <= scale * SYM[precision] * F[check])
 
 
 def depth(ion, cells):
@@ -39,7 +54,8 @@ def test_rabbit_hole(B, orc, axis, precision):
     ot, p = orc.Tree(w), orc.params_for(w)
     targets = cells.ravel()
     checked, worst = sampled_check(F, ion, targets, uniform_neighbours(targets, w.N),
-                                   lambda c: ot.solve_pass(p, targets=c), RTOL[precision])
+                                   lambda c: ot.solve_pass(p, targets=c), RTOL[precision], KAPPA[precision],
+                                   lambda c: ot.free_flux(p, targets=c))
     assert checked > targets.size // 2
     F_o, _, ion_o = ot.solve_pass(p, targets=targets)
     full = np.zeros(w.N ** 3, dtype=np.uint8)
@@ -58,14 +74,11 @@ def test_two_sources_one_pass(B, orc, precision):
     w = two_sources_cloud(64, nside=2, theta_lim=0.5)
     F, e, ion = gpu_solve(B, w, precision)
     N = w.N
-    Fc, ic = F.reshape(N, N, N), ion.reshape(N, N, N)
-    assert np.array_equal(ic, mirror_xy(ic))
-    lit = Fc > 0
-    assert np.all(np.abs(Fc - mirror_xy(Fc))[lit] <= SYM[precision] * Fc[lit])
+    assert_mirror_symmetric(F.reshape(N, N, N), ion.reshape(N, N, N), precision)
     targets = mid_plane(N)
-    sampled_check(F, ion, targets, uniform_neighbours(targets, N),
-                  lambda c: oracle_pass("scene", {"fn": "two_sources_cloud", "kw": dict(N=64, nside=2, theta_lim=0.5)},
-                                        c, nproc=8), RTOL[precision])
+    spec = {"fn": "two_sources_cloud", "kw": dict(N=64, nside=2, theta_lim=0.5)}
+    sampled_check(F, ion, targets, uniform_neighbours(targets, N), lambda c: oracle_pass("scene", spec, c, nproc=8),
+                  RTOL[precision], KAPPA[precision], lambda c: oracle_free("scene", spec, c, nproc=8))
 
 
 def test_two_sources_converged_symmetric(B):
@@ -78,7 +91,4 @@ def test_two_sources_converged_symmetric(B):
                                     theta_if=0.5, nside=2, precision=precision, max_iter=12, eps_lim=1e-2)
         torch.cuda.synchronize()
         assert dl < 1e-2 and it < 12
-        ec, ic = e.cpu().numpy(), ion.cpu().numpy()
-        assert np.array_equal(ic, mirror_xy(ic))
-        lit = ec > 0
-        assert np.all(np.abs(ec - mirror_xy(ec))[lit] <= 10 * SYM[precision] * ec[lit])
+        assert_mirror_symmetric(e.cpu().numpy(), ion.cpu().numpy(), precision, scale=10.0)

@@ -1,5 +1,8 @@
 """Continuous batching on the GPU: every request's result is the same alone
-and in the mix (tr_walk_sweep_batch through the serving loop)."""
+and in the mix (tr_walk_sweep_batch through the serving loop; to rounding in
+FP64, whose deposits are FP64 atomics in any order, bit for bit in the FP32
+forms), and the footprint that admission charges covers what a request
+really allocates on the device."""
 import math
 
 import numpy as np
@@ -10,7 +13,7 @@ from workloads import PC_CM, lognormal_density, uniform_sources
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {0: 1e-12, 1: 1e-6}
+RTOL = {0: 1e-12, 1: 0.0, 2: 0.0}
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +49,7 @@ def alone(B, r, precision):
     return F.cpu().numpy(), ion.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_mix_equals_alone(B, precision):
     from paper_2105_09644_gb300.serving import Server
     reqs = requests()
@@ -86,3 +89,36 @@ def test_batch_entry_point_ranges(B):
     torch.cuda.synchronize()
     assert np.allclose(outs[0].cpu().numpy(), F0, rtol=1e-6, atol=0)
     assert np.allclose(outs[1].cpu().numpy(), F1, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_footprint_covers_allocations(B, precision):
+    """Device memory taken by one request (inputs, outputs, tree, ray
+    tables) against footprint_bytes: never more, and not wildly less."""
+    import torch
+    from paper_2105_09644_gb300.serving import footprint_bytes
+    for N, S in ((32, 10), (64, 300), (128, 1000)):
+        box = 4.0 * PC_CM
+        rho = lognormal_density(N, 5)
+        xyz, q = uniform_sources(S, box, 6, 46.0, 48.0)
+        p = B.tr_params_default(precision=precision)
+
+        def one():
+            d = [torch.from_numpy(a).cuda() for a in (rho, xyz, q)]
+            out = [torch.empty((N,) * 3, dtype=torch.float64, device="cuda") for _ in range(2)]
+            out.append(torch.empty((N,) * 3, dtype=torch.uint8, device="cuda"))
+            t = B.tr_build_tree(B.make_grid(d[0], box / N), B.make_sources(d[1], d[2]), p)
+            torch.cuda.synchronize()
+            return d, out, t
+        keep = one()                             # the node->ray table of N_side 2 is built and cached here
+        del keep
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free0 = torch.cuda.mem_get_info()[0]
+        keep = one()
+        used = free0 - torch.cuda.mem_get_info()[0]
+        fp = footprint_bytes(N, precision, S)
+        assert used <= fp <= 1.5 * used + (32 << 20), (N, used, fp)
+        del keep
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()

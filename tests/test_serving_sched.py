@@ -20,7 +20,7 @@ def drive(sched, reqs, rng):
             sched.submit(pending.pop(0))
         sched.admit(now)
         assert sched.in_use <= sched.budget
-        assert sched.in_use == sum(footprint_bytes(r.N, sched.precision) for r in sched.active)
+        assert sched.in_use == sum(r.footprint for r in sched.active)
         peak = max(peak, sched.in_use)
         slices = sched.plan()
         for r, f, c in slices:
@@ -61,8 +61,8 @@ def test_small_requests_go_first():
 
 
 def test_oversized_request_is_refused():
-    sched = Scheduler(footprint_bytes(16, 1), tick_targets=1000)
-    sched.submit(fake(0, 32, 0.0))
+    sched = Scheduler(footprint_bytes(32, 1), tick_targets=1000)
+    sched.submit(fake(0, 128, 0.0))
     with pytest.raises(ValueError):
         sched.admit(0.0)
 
