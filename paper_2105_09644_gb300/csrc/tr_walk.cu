@@ -661,97 +661,111 @@ __device__ __forceinline__ double alpha_at(const WalkArgs& a, const double* ba, 
     return (double)(bin_value_f<MODE>(ba + i, inv_scale) * __ldg(a.inv_volf + i));
 }
 
-// Far-to-near sweep of one ray (Sec. 2.5) straight from its bins: ba, be, bee
-// are the ray's N_R slots of alpha, eps and e (raw deposits).  Rays without
-// emission cost only the scan for it.  The eps slots are overwritten with the
-// photon rates Phi_j (FP64).  All of it is FP64 arithmetic (the FP32 forms'
-// coefficients widened), counted to few FP64 instructions per segment and
-// source: GB300 issues FP64 at 1/64 of the FP32 rate.  The loss of source j
+// Far-to-near sweep of one ray (Sec. 2.5) straight from its bins, by a pair
+// of lanes of one warp (gl = 0, 1; gmask = the pair): ba, be, bee are the
+// ray's N_R slots of alpha, eps and e (raw deposits).  Lane gl owns the
+// ray's source points j with j % 2 == gl and keeps their photon rates Phi_j
+// (FP64, in place of their eps slots); the total flux of a segment (zeta_s,
+// zeta_d) is summed over the pair with one shuffle.  All of it is FP64
+// arithmetic (the FP32 forms' coefficients widened).  The loss of source j
 // over segment i is R_ij = (alpha_i + alpha_{i+1}) G_ij zeta_d zeta_s with
-// G_ij = (1/2) dV_ij zeta_g,ij (Eq. 14-16), and Phi_j <- max(Phi_j - R_ij, 0)
-// (Eq. 13) is one FMA and a test of the sign bit.
+// G_ij = (1/2) dV_ij zeta_g,ij (Eq. 14-16), and Phi_j <- max(Phi_j - R_ij,
+// 0) (Eq. 13) is one FMA and a test of the sign bit.  GB300 issues FP64 at
+// 1/64 of the FP32 rate and a deep chain of dependent FP64 operations per
+// segment sets the sweep's time, so the pair halves that chain.  Rays
+// without emission cost only the scan for it.  Both lanes return F_0.
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 
+constexpr uint64_t EVEN_BITS = 0x5555555555555555ull;   // bits j with j % 2 == 0
+
 template <int MODE>
-__device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, const double* bee, const Scales& sc) {
+__device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, const double* bee, const Scales& sc,
+                            int gl, unsigned gmask) {
     const int nr = a.nr;
     uint64_t m0 = 0, m1 = 0;
-    for (int j = 1; j < nr; ++j) {
-        if (bin_nonzero<MODE>(be + j)) {
-            if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64);
-        }
+    for (int j = 2 - gl; j < nr; j += 2) {                    // lane gl scans its parity (j >= 1)
+        if (bin_nonzero<MODE>(be + j)) { if (j < 64) m0 |= 1ull << j; else m1 |= 1ull << (j - 64); }
     }
+    m0 |= __shfl_xor_sync(gmask, m0, 1);
+    m1 |= __shfl_xor_sync(gmask, m1, 1);
     if (!(m0 | m1)) return 0.0;
+    const uint64_t sel = EVEN_BITS << gl;                     // the lane's parity (64 is even)
+    uint64_t o0 = m0 & sel, o1 = m1 & sel;                    // own live sources
     const double inv4pi = 1.0 / (4.0 * PI_D);
-    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; be[j] = bin_value<MODE>(be + j, sc.eps) * inv4pi; }
-    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; be[j] = bin_value<MODE>(be + j, sc.eps) * inv4pi; }
+    for (uint64_t w = o0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; be[j] = bin_value<MODE>(be + j, sc.eps) * inv4pi; }
+    for (uint64_t w = o1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; be[j] = bin_value<MODE>(be + j, sc.eps) * inv4pi; }
     double* ph = be;                                              // Eq. 12
+    __syncwarp(gmask);
     const float ia = 1.0f / sc.a, ie = 1.0f / sc.e;
     const int jtop = m1 ? 64 + 63 - __clzll((long long)m1) : 63 - __clzll((long long)m0);
     if (!bee && __popcll((long long)m0) + __popcll((long long)m1) == 1) {
         // a lone source and no e: zeta_s = zeta_d = 1 on every segment, every
         // R_ij >= 0, so clipping once at the end equals clipping per segment
         // (Eq. 13): Phi_0 = max(Phi_j - sum_i bin_i HT[j][i], 0), an FP64 dot
-        // product (two accumulators to halve the dependency chain)
+        // product split over the pair
         const double* h = a.HT + (size_t)jtop * nr;
-        double s0 = 0.0, s1 = 0.0;
-        int i = 0;
-        for (; i + 1 <= jtop; i += 2) {
+        double s0 = 0.0;
+        for (int i = gl; i <= jtop; i += 2)
             s0 = fma((double)(MODE == 0 ? ba[i] : (double)bin_value_f<MODE>(ba + i, ia)), __ldg(h + i), s0);
-            s1 = fma((double)(MODE == 0 ? ba[i + 1] : (double)bin_value_f<MODE>(ba + i + 1, ia)), __ldg(h + i + 1), s1);
-        }
-        if (i <= jtop) s0 = fma((double)(MODE == 0 ? ba[i] : (double)bin_value_f<MODE>(ba + i, ia)), __ldg(h + i), s0);
-        const double phi = ph[jtop] - (s0 + s1);
+        s0 += __shfl_xor_sync(gmask, s0, 1);
+        const double phi = ph[jtop] - s0;
         return positive(phi) ? phi * __ldg(a.inv_r2 + jtop) : 0.0;
     }
     double a_hi = alpha_at<MODE>(a, ba, jtop, ia);
-    for (int i = jtop - 1; i >= 0 && (m0 | m1); --i) {
-        const double a_lo = alpha_at<MODE>(a, ba, i, ia);
+    for (int i = jtop - 1; i >= 0; --i) {
         const int b = i + 1;                                      // sources strictly beyond r_i
-        const uint64_t a0 = (b < 64) ? (m0 & (~0ull << b)) : 0ull;
-        const uint64_t a1 = (b <= 64) ? m1 : (m1 & (~0ull << (b - 64)));
-        if (a0 | a1) {
-            const double A = a_lo + a_hi;                         // twice the mean coefficient
-            const double* g = a.G + (size_t)i * nr;
-            if (!bee && __popcll((long long)a0) + __popcll((long long)a1) == 1) {
-                // one source on the segment: zeta_s = 1, and zeta_d = 1 without e
+        const uint64_t a0 = (b < 64) ? (o0 & (~0ull << b)) : 0ull;
+        const uint64_t a1 = (b <= 64) ? o1 : (o1 & (~0ull << (b - 64)));
+        const int own = __popcll((long long)a0) + __popcll((long long)a1);
+        const int cnt = own + __shfl_xor_sync(gmask, own, 1);
+        if (cnt == 0) {                                           // nothing left beyond r_i on the ray
+            if (!__any_sync(gmask, (o0 | o1) != 0ull)) break;
+            a_hi = alpha_at<MODE>(a, ba, i, ia);
+            continue;
+        }
+        const double a_lo = alpha_at<MODE>(a, ba, i, ia);
+        const double A = a_lo + a_hi;                             // twice the mean coefficient
+        if (!bee && cnt == 1) {
+            // one source on the segment: zeta_s = 1, and zeta_d = 1 without e
+            if (own) {
                 const int j = a0 ? __ffsll((long long)a0) - 1 : 64 + __ffsll((long long)a1) - 1;
-                const double np = fma(-A, __ldg(g + j), ph[j]);   // Eq. 13-14
+                const double np = fma(-A, __ldg(a.G + (size_t)i * nr + j), ph[j]);   // Eq. 13-14
                 if (positive(np)) ph[j] = np;
-                else { ph[j] = 0.0; if (j < 64) m0 &= ~(1ull << j); else m1 &= ~(1ull << (j - 64)); }
-            } else {
-                const double* id2 = a.ID2 + (size_t)i * nr;
-                const double* gi = a.GI + (size_t)i * nr;
-                double Ftot = 0.0;                                // Eq. 11 at the segment midpoint
-                for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Ftot = fma(ph[j], __ldg(id2 + j), Ftot); }
-                for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Ftot = fma(ph[j], __ldg(id2 + j), Ftot); }
-                if (positive(Ftot)) {
-                    const double inv_F = recip_nr(Ftot);
-                    double zd = 1.0;                              // Eq. 17
-                    if (bee) {
-                        const double ev = alpha_at<MODE>(a, bee, i + 1, ie);
-                        if (positive(ev)) zd = fmin(2.0, Ftot * recip_nr(ev));
-                    }
-                    const double cf = A * zd * inv_F;             // zeta_s = F_j / Ftot (Eq. 16)
-                    for (uint64_t w = a0; w; w &= w - 1) {
-                        const int j = __ffsll((long long)w) - 1;
-                        const double np = fma(-cf * __ldg(gi + j), ph[j], ph[j]);   // Eq. 13-14
-                        if (positive(np)) ph[j] = np; else { ph[j] = 0.0; m0 &= ~(1ull << j); }
-                    }
-                    for (uint64_t w = a1; w; w &= w - 1) {
-                        const int j = 64 + __ffsll((long long)w) - 1;
-                        const double np = fma(-cf * __ldg(gi + j), ph[j], ph[j]);
-                        if (positive(np)) ph[j] = np; else { ph[j] = 0.0; m1 &= ~(1ull << (j - 64)); }
-                    }
+                else { ph[j] = 0.0; if (j < 64) o0 &= ~(1ull << j); else o1 &= ~(1ull << (j - 64)); }
+            }
+        } else {
+            const double* id2 = a.ID2 + (size_t)i * nr;
+            const double* gi = a.GI + (size_t)i * nr;
+            double Fl = 0.0;                                      // Eq. 11 at the segment midpoint
+            for (uint64_t w = a0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; Fl = fma(ph[j], __ldg(id2 + j), Fl); }
+            for (uint64_t w = a1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; Fl = fma(ph[j], __ldg(id2 + j), Fl); }
+            const double Ftot = Fl + __shfl_xor_sync(gmask, Fl, 1);
+            if (positive(Ftot)) {
+                const double inv_F = recip_nr(Ftot);
+                double zd = 1.0;                                  // Eq. 17
+                if (bee) {
+                    const double ev = alpha_at<MODE>(a, bee, i + 1, ie);
+                    if (positive(ev)) zd = fmin(2.0, Ftot * recip_nr(ev));
+                }
+                const double cf = A * zd * inv_F;                 // zeta_s = F_j / Ftot (Eq. 16)
+                for (uint64_t w = a0; w; w &= w - 1) {
+                    const int j = __ffsll((long long)w) - 1;
+                    const double np = fma(-cf * __ldg(gi + j), ph[j], ph[j]);   // Eq. 13-14
+                    if (positive(np)) ph[j] = np; else { ph[j] = 0.0; o0 &= ~(1ull << j); }
+                }
+                for (uint64_t w = a1; w; w &= w - 1) {
+                    const int j = 64 + __ffsll((long long)w) - 1;
+                    const double np = fma(-cf * __ldg(gi + j), ph[j], ph[j]);
+                    if (positive(np)) ph[j] = np; else { ph[j] = 0.0; o1 &= ~(1ull << (j - 64)); }
                 }
             }
         }
         a_hi = a_lo;
     }
     double F0 = 0.0;                                              // Eq. 10-11 at r = 0
-    for (uint64_t w = m0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
-    for (uint64_t w = m1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
-    return F0;
+    for (uint64_t w = o0; w; w &= w - 1) { const int j = __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
+    for (uint64_t w = o1; w; w &= w - 1) { const int j = 64 + __ffsll((long long)w) - 1; F0 = fma(ph[j], __ldg(a.inv_r2 + j), F0); }
+    return F0 + __shfl_xor_sync(gmask, F0, 1);
 }
 
 // The sweep of the FP32 form.  The deposits (alpha, e) and the geometric
@@ -891,11 +905,16 @@ __device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, 
     const int nr = a.nr, tid = threadIdx.x;
     double Fk = 0.0;
     if (MODE != 2) {
-        // consecutive rays on consecutive lanes: GB300 charges an FP64 warp
+        // a pair of consecutive lanes per ray: GB300 charges an FP64 warp
         // instruction in full however few lanes it has, so the FP64 work is
-        // packed into as few warps as there are rays / 32
-        for (int k = tid; k < a.npix; k += NT)
-            Fk += sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr, sc);
+        // packed onto consecutive lanes
+        const int gl = tid & 1, lane = tid & 31;
+        const unsigned gmask = 3u << (lane & ~1);
+        for (int k = tid >> 1; k < a.npix; k += NT / 2) {
+            const double f = sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr,
+                                             sc, gl, gmask);
+            if (gl == 0) Fk += f;
+        }
     } else {
         const int gl = tid % SG, lane = tid & 31;
         const unsigned gmask = ((1u << SG) - 1u) << (lane & ~(SG - 1));
@@ -978,7 +997,12 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
     constexpr int NW = NT / 32, P = NT / 8;
     constexpr bool DUMP = OUT == OUT_DUMP, CD = OUT == OUT_CD;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_wcnt[NW], s_bcnt[NW], s_pcnt[NW];
+    // per step: stack pushes, and spread nodes (high word) with their
+    // (node, ray) pairs (low word), reserved by one atomic per warp; two
+    // sets, by step parity, so that a set is cleared a step after its use
+    __shared__ int s_push[2];
+    __shared__ unsigned long long s_spread[2];
+    __shared__ int s_over;
     __shared__ double s_red[NW];
     __shared__ unsigned int s_q;
     __shared__ int s_j;
@@ -1080,8 +1104,11 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
         const real hts = real(0.5) * (real)ts;
         const real px = (real)tx + hts, py = (real)ty + hts, pz = (real)tz + hts;
         for (int b = tid; b < nq * nbins; b += NT) bins_a[b] = 0.0;
-        if (tid == 0) { stack[0] = 0u; s_nacc = 0; }               // the root, opened
-        int top = 1, max_top = 1;
+        if (tid == 0) {                                          // the root, opened
+            stack[0] = 0u; s_nacc = 0;
+            s_push[0] = s_push[1] = 0; s_spread[0] = s_spread[1] = 0ull; s_over = 0;
+        }
+        int top = 1, max_top = 1, par = 0;
         bool overflow = false;
         __syncthreads();
         // corner of symmetry: the original and its 7 mirror images (bit k of
@@ -1215,7 +1242,10 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                     }
                 }
             }
-            // block-wide offsets of the pushes and of the nodes to spread
+            // stack slots of the pushes and spread-list slots of the nodes to
+            // spread: one shared atomic per warp reserves them (the order of
+            // the warps' blocks is immaterial: fixed-point or FP64 atomic
+            // deposits, accepted nodes a set)
             const unsigned om = __ballot_sync(FULL, action == 1);
             const unsigned bm = __ballot_sync(FULL, spread);
             // work items of this thread's node: (ray, point) triples (FP64) or rays (FP32)
@@ -1225,24 +1255,25 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                 const int v = __shfl_up_sync(FULL, incl, o);
                 if (lane >= o) incl += v;
             }
-            if (lane == 31) s_pcnt[wid] = incl;
-            if (lane == 0) { s_wcnt[wid] = __popc(om); s_bcnt[wid] = __popc(bm); }
-            __syncthreads();                                     // per-warp counts visible
-            int obase = 0, ototal = 0, nbase = 0, ntotal = 0, pbase = 0, ptotal = 0;
-            for (int w = 0; w < NW; ++w) {
-                const int oc = s_wcnt[w], bc = s_bcnt[w], pcw = s_pcnt[w];
-                if (w < wid) { obase += oc; nbase += bc; pbase += pcw; }
-                ototal += oc; ntotal += bc; ptotal += pcw;
+            const int wpairs = __shfl_sync(FULL, incl, 31);      // the warp's pairs
+            int obase = 0;
+            unsigned long long nbp = 0ull;
+            if (lane == 0) {
+                if (om) obase = atomicAdd(&s_push[par], __popc(om));
+                if (bm) nbp = atomicAdd(&s_spread[par], ((unsigned long long)__popc(bm) << 32) |
+                                                          (unsigned long long)(unsigned)wpairs);
             }
-            if (top + ototal > a.stack_cap) overflow = true;     // same value in every thread
-            if (!overflow) {
-                if (action == 1) stack[top + obase + __popc(om & lanemask_lt)] = ((uint32_t)lev << 27) | mort;
-                if (spread) {
-                    const int k = nbase + __popc(bm & lanemask_lt);
-                    s_node[k] = node;
-                    s_pair0[k] = pbase + incl - pc;
-                }
-                if (tid == 0) s_pair0[ntotal] = ptotal;
+            obase = __shfl_sync(FULL, obase, 0);
+            nbp = __shfl_sync(FULL, nbp, 0);
+            if (action == 1) {
+                const int slot = top + obase + __popc(om & lanemask_lt);
+                if (slot < a.stack_cap) stack[slot] = ((uint32_t)lev << 27) | mort;
+                else s_over = 1;                                 // never written past
+            }
+            if (spread) {
+                const int k = (int)(nbp >> 32) + __popc(bm & lanemask_lt);
+                s_node[k] = node;
+                s_pair0[k] = (int)(nbp & 0xffffffffull) + incl - pc;
             }
             if (action == 2) {
                 ++cnt.acc;
@@ -1252,6 +1283,12 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                 }
             }
             __syncthreads();                                     // pushes and spread list visible
+            const int ototal = s_push[par];
+            const unsigned long long sp = s_spread[par];
+            const int ntotal = (int)(sp >> 32), ptotal = (int)(sp & 0xffffffffull);
+            overflow = s_over != 0;                              // same value in every thread
+            if (tid == 0) { s_push[par ^ 1] = 0; s_spread[par ^ 1] = 0ull; }   // read by all a step ago
+            par ^= 1;
             if (overflow) break;
             // spread the step's nodes.  FP64 form: each thread takes a contiguous
             // run of (node, table entry, radial point) triples, so that every
@@ -1271,7 +1308,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                         RadialSpread<MODE> n = s_node[k];
                         const int li = p0 - s_pair0[k];
                         int e = li / n.npts, j = li - e * n.npts;
-                        int ne_k = (s_pair0[k + 1] - s_pair0[k]) / n.npts;
+                        int ne_k = ((k + 1 < ntotal ? s_pair0[k + 1] : ptotal) - s_pair0[k]) / n.npts;
                         uint32_t en = __ldg(a.tent + n.off + e);
                         int b0 = (int)(en >> 16) * nr + n.lo;
                         real wk = (real)(en & 0xffffu) * inv_m3;
@@ -1288,7 +1325,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                                     ++k;
                                     n = s_node[k];
                                     e = 0;
-                                    ne_k = (s_pair0[k + 1] - s_pair0[k]) / n.npts;
+                                    ne_k = ((k + 1 < ntotal ? s_pair0[k + 1] : ptotal) - s_pair0[k]) / n.npts;
                                 }
                                 en = __ldg(a.tent + n.off + e);
                                 b0 = (int)(en >> 16) * nr + n.lo;
@@ -1308,9 +1345,9 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
                             if (s_pair0[mid] <= p0) k = mid; else hi = mid - 1;
                         }
                         RadialSpread<MODE> n = s_node[k];
-                        int kend = s_pair0[k + 1];
+                        int kend = k + 1 < ntotal ? s_pair0[k + 1] : ptotal;
                         for (int p = p0; p < p1; ++p) {
-                            if (p >= kend) { ++k; n = s_node[k]; kend = s_pair0[k + 1]; }
+                            if (p >= kend) { ++k; n = s_node[k]; kend = k + 1 < ntotal ? s_pair0[k + 1] : ptotal; }
                             const uint32_t en = __ldg(a.tent + n.off + (p - s_pair0[k]));
                             const int b0 = (int)(en >> 16) * nr + n.lo;
                             const real wk = (real)(en & 0xffffu) * inv_m3;

@@ -68,21 +68,25 @@ def num_points(N: int, eta_r: int = 2) -> int:
 
 
 def footprint_bytes(N: int, precision: int, n_sources: int = 1000, eta_r: int = 2) -> int:
-    """Device bytes a request holds while resident: its tree (node records
-    and build sums; the FP32 forms keep the FP64 tree beside the FP32 one),
-    mapped emission, ray tables, inputs and outputs, each allocation rounded
-    up to 2 MiB (the device allocator's granularity for large blocks).  The
-    node->ray table of each N_side is shared by all requests and is not
-    counted here."""
+    """Device bytes a request holds while resident, counted per allocation
+    and each rounded up to 2 MiB (an upper bound: the device allocator
+    rounds large allocations to 2 MiB and packs small ones together): the
+    library's tree (node records and build sums; the FP32 forms keep the
+    FP64 tree beside the FP32 one, and a word for its error bound), mapped
+    emission, status words and counters, the job record, the twelve ray
+    tables; and the request's inputs and outputs.  The node->ray table of
+    each N_side is shared by all requests and is not counted here."""
     def rounded(b):
-        return -(-int(b) // (2 << 20)) * (2 << 20)
+        return max(1, -(-int(b) // (2 << 20))) * (2 << 20)
     n_nodes = ((1 << (3 * (int(math.log2(N)) + 1))) - 1) // 7
     cells = N ** 3
     nr = num_points(N, eta_r)
-    tree = [n_nodes * 64, n_nodes * 24] if precision == 0 else [n_nodes * 32, n_nodes * 12, n_nodes * 64, n_nodes * 24]
-    tree += [cells * 8, 7 * nr * nr * 8 + 5 * nr * 8, 4096]                # emission, ray tables, small state
-    io = [cells * 8, n_sources * 32, cells * 8, cells * 8, cells]           # n_H, sources, F, e, ion
-    return sum(rounded(b) for b in tree + io)
+    lib = [n_nodes * 64, n_nodes * 24] if precision == 0 else [n_nodes * 32, n_nodes * 12, n_nodes * 64,
+                                                                n_nodes * 24, 4]
+    lib += [cells * 8, 16, 64, 4, 512]                                     # emission, status, stats, counter, job
+    lib += [nr * 8] * 5 + [nr * nr * 8] * 7                                # ray tables
+    io = [cells * 8, n_sources * 32, cells * 8, cells * 8, cells]          # n_H, sources, F, e, ion
+    return sum(rounded(b) for b in lib + io)
 
 
 class Scheduler:

