@@ -774,13 +774,12 @@ __device__ double sweep_ray(const WalkArgs& a, const double* ba, double* be, con
 // L_j = sum of R_ij are carried as unevaluated sums of two FP32 numbers
 // (hi + lo, about 48 significant bits; L by compensated addition), so that
 // the per-segment work needs no FP64 instruction -- on GB300 FP64 runs at
-// 1/54 of the FP32 rate and would make the sweep cost grow with the number
+// 1/64 of the FP32 rate and would make the sweep cost grow with the number
 // of sources on a ray.  A source is spent when L_j reaches E_j
 // (Phi = max(E - L, 0), Eq. 13).  The cancellation Phi_j = E_j - L_j that
 // decides the flux near the ionisation front, the flux F_0 (Eq. 10-11) and
 // hence the ionised/neutral classification are done in FP64 at the end of
-// the ray.  E_j lives in the eps slot of point j and L_j in the alpha slot
-// of point j, which the sweep has consumed by the time source j starts.
+// the ray.
 __device__ __forceinline__ float2 two_sum(float a, float b) {    // Knuth: a + b = s + e exactly
     const float s = a + b;
     const float bp = s - a;
@@ -896,35 +895,216 @@ __device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* b
     return F0;
 }
 
-// Sum over the rays of one target (Eq. 18): FP64 sweep (FP64 form and FP32 +
-// FP64-sweep form) one thread per ray, double-FP32 sweep one group of SG
-// lanes per ray.
+// Per-target ray tables for the double-FP32 sweep, in shared scratch:
+// order[npix] (u16, the ray of each rank), off[npix] (u16, first lane of each
+// lane group), cnt[npix] (u8, emitting points of each ray), then four ints:
+// the rays with sources, the lanes of the groups, the rays swept by pairs,
+// the emitting points of all rays.
+constexpr int MAX_NPIX = 12 * 8 * 8;                  // N_side <= 8
+constexpr int GROUP_MAX = 32;                         // rays with more points go to lane pairs
+constexpr int GROUP_MEAN_MAX = 8;                     // lane groups while a lit ray has at most this many points on average
+__host__ __device__ constexpr size_t sweep_hdr_offset(int npix) { return ((size_t)npix * 5 + 3) & ~(size_t)3; }
+__host__ __device__ constexpr size_t sweep_scratch_bytes(int npix) { return sweep_hdr_offset(npix) + 16; }
+
+// Lanes given to a ray with c emitting points in a lane group: the next
+// power of two.
+__device__ __forceinline__ int group_width(int c) { return c <= 1 ? c : 1 << (32 - __clz(c - 1)); }
+
+// Ranks the rays of a target for the double-FP32 sweep, ties by ray index:
+// first the rays with more than GROUP_MAX emitting points (swept by lane
+// pairs), then the others by decreasing lane-group width, each group's first
+// lane recorded (groups sorted by decreasing power-of-two width never
+// straddle a warp), rays without sources last.  Deterministic: the ranks
+// depend only on the bins.
+template <int NT>
+__device__ __forceinline__ void rank_rays(const WalkArgs& a, const double* bins_eps, unsigned char* scratch) {
+    const int npix = a.npix, nr = a.nr, tid = threadIdx.x;
+    uint16_t* order = reinterpret_cast<uint16_t*>(scratch);
+    uint16_t* off = order + npix;
+    uint8_t* cnt = reinterpret_cast<uint8_t*>(off + npix);
+    int* hdr = reinterpret_cast<int*>(scratch + sweep_hdr_offset(npix));
+    for (int k = tid; k < npix; k += NT) {
+        const double* be = bins_eps + (size_t)k * nr;
+        int c = 0;
+        for (int j = 1; j < nr; ++j) c += bin_nonzero<1>(be + j) ? 1 : 0;
+        cnt[k] = (uint8_t)c;
+    }
+    __syncthreads();                                          // counts visible
+    auto key = [](int c) { return c > GROUP_MAX ? 2 * GROUP_MAX : group_width(c); };
+    for (int k = tid; k < npix; k += NT) {
+        const int ck = key(cnt[k]);
+        int rank = 0, lanes = 0, nz = 0, total = 0, nbig = 0, npts = 0;
+        for (int k2 = 0; k2 < npix; ++k2) {
+            const int c2 = cnt[k2], key2 = key(c2);
+            const bool before = key2 > ck || (key2 == ck && k2 < k);
+            const int w2 = c2 > GROUP_MAX ? 0 : key2;
+            rank += before ? 1 : 0;
+            lanes += before ? w2 : 0;
+            total += w2;
+            nz += c2 > 0 ? 1 : 0;
+            nbig += c2 > GROUP_MAX ? 1 : 0;
+            npts += c2;
+        }
+        order[rank] = (uint16_t)k;
+        off[rank] = (uint16_t)lanes;
+        if (k == 0) { hdr[0] = nz; hdr[1] = total; hdr[2] = nbig; hdr[3] = npts; }
+    }
+    __syncthreads();                                          // ranks visible
+}
+
+// Double-FP32 sweep of the rays of a target with 1..GROUP_MAX emitting
+// points, a lane per point (a lane per point spends less on bookkeeping than
+// a lane pair looping over a ray's points, but idles on the points not yet
+// reached; it wins while rays carry few points): the rays' lane groups (rank order, group_width
+// lanes each) are laid end to end over the CTA's warps, and lane `slot` of a
+// ray's group keeps the ray's slot-th emitting point in registers: its
+// budget E_j = eps_j / 4pi and running loss L_j as unevaluated FP32 pairs
+// (Eq. 12-14, as in sweep_ray_group), with the segments swept far to near in
+// lockstep over the warp.  A segment's total flux (zeta_s, zeta_d; Eq.
+// 16-17) is a butterfly sum over the group, the same in every lane of it.  A
+// ray with one point and no e has zeta_s = zeta_d = 1, R_ij = A_i G_ij.
+// Each group's first lane returns its ray's F_0 (FP64) in the sum.
+template <int NT>
+__device__ double sweep_groups(const WalkArgs& a, const double* bins_a, const double* bins_eps, const double* bins_e,
+                               const Scales& sc, const unsigned char* scratch) {
+    const int npix = a.npix, nr = a.nr, lane = threadIdx.x & 31;
+    const uint16_t* order = reinterpret_cast<const uint16_t*>(scratch);
+    const uint16_t* off = order + npix;
+    const uint8_t* cnt = reinterpret_cast<const uint8_t*>(off + npix);
+    const int* hdr = reinterpret_cast<const int*>(scratch + sweep_hdr_offset(npix));
+    const int nz = hdr[0], T = hdr[1], nbig = hdr[2];
+    const double inv4pi = 1.0 / (4.0 * PI_D);
+    const float ia = 1.0f / sc.a, ie = 1.0f / sc.e;
+    double Fk = 0.0;
+    for (int base = threadIdx.x & ~31; base < T; base += NT) {  // warp-uniform
+        const int p = base + lane;
+        const bool in = p < T;
+        int g = nbig;                                         // the last rank whose group starts at or before p
+        if (in) {
+            int hi = nz - 1;
+            while (g < hi) {
+                const int mid = (g + hi + 1) >> 1;
+                if ((int)off[mid] <= p) g = mid; else hi = mid - 1;
+            }
+        }
+        const int k = in ? order[g] : 0;
+        const int c = in ? cnt[k] : 0;
+        const int w = group_width(c);
+        const int slot = in ? p - (int)off[g] : 0;
+        const double* ba = bins_a + (size_t)k * nr;
+        const double* be = bins_eps + (size_t)k * nr;
+        const double* bee = bins_e ? bins_e + (size_t)k * nr : nullptr;
+        int jA = 0, jtop = 0;                                 // own point, the ray's farthest
+        if (in) {
+            int n = 0;
+            for (int j = 1; j < nr; ++j)
+                if (bin_nonzero<1>(be + j)) {
+                    if (n == slot) jA = j;
+                    jtop = j;
+                    ++n;
+                }
+        }
+        const bool vA = slot < c;
+        float2 EA = make_float2(0.f, 0.f), LA = EA;
+        if (vA) { const double v = bin_value<1>(be + jA, sc.eps) * inv4pi; EA.x = (float)v; EA.y = (float)(v - (double)EA.x); }
+        bool sA = !vA;                                        // spent, or no point
+        const bool single = c == 1 && !bee;                   // zeta_s = zeta_d = 1 throughout
+        const int wmax = __reduce_max_sync(FULL, (unsigned)w);
+        const int itop = __reduce_max_sync(FULL, (unsigned)jtop);
+        float a_hi = in ? bin_value_f<1>(ba + itop, ia) * __ldg(a.inv_volf + itop) : 0.f;
+        for (int i = itop - 1; i >= 0; --i) {
+            if (!__any_sync(FULL, !sA)) break;                // every point of the warp spent
+            const float a_lo = in ? bin_value_f<1>(ba + i, ia) * __ldg(a.inv_volf + i) : 0.f;
+            const bool live = !sA && jA > i;
+            const float ph = live ? phi_f(EA, LA) : 0.f;
+            float Fl = live ? ph * __ldg(a.ID2f + (size_t)i * nr + jA) : 0.f;   // Eq. 11 at the segment midpoint
+            for (int o = 1; o < wmax; o <<= 1) {
+                const float t = __shfl_xor_sync(FULL, Fl, o);
+                if (o < w) Fl += t;
+            }
+            if (live) {                                       // then Fl > 0
+                const float A = a_lo + a_hi;                  // G carries the 1/2 of the mean
+                float R;
+                if (single) {
+                    R = A * __ldg(a.Gf + (size_t)i * nr + jA);                       // Eq. 14
+                } else {
+                    float zd = 1.f;                           // Eq. 17
+                    if (bee) {
+                        const float ev = bin_value_f<1>(bee + i + 1, ie) * __ldg(a.inv_volf + i + 1);
+                        if (ev > 0.f) zd = fminf(2.f, __fdividef(Fl, ev));
+                    }
+                    R = __fdividef(A * zd, Fl) * (__ldg(a.GIf + (size_t)i * nr + jA) * ph);   // zeta_s = F_j / Ftot
+                }
+                const float2 t = two_sum(LA.x, R);            // compensated L += R
+                const float2 Ln = two_sum(t.x, t.y + LA.y);
+                if (phi_f(EA, Ln) > 0.f) LA = Ln; else sA = true;   // spent: Phi = 0 (Eq. 13)
+            }
+            a_hi = a_lo;
+        }
+        double F0 = 0.0;                                      // Eq. 10-11 at r = 0, in FP64
+        if (!sA) {
+            const double phi = ((double)EA.x + (double)EA.y) - ((double)LA.x + (double)LA.y);
+            if (phi > 0.0) F0 = fma(phi, __ldg(a.inv_r2 + jA), F0);
+        }
+        for (int o = 1; o < wmax; o <<= 1) {
+            const double t = __shfl_xor_sync(FULL, F0, o);
+            if (o < w) F0 += t;
+        }
+        if (in && slot == 0) Fk += F0;
+    }
+    return Fk;
+}
+
+// Sum over the rays of one target (Eq. 18).  FP64 sweeps (FP64 form and
+// FP32 + FP64-sweep form): a pair of consecutive lanes per ray -- GB300
+// charges an FP64 warp instruction in full however few lanes it has, so the
+// FP64 work is packed onto consecutive lanes.  Double-FP32 sweep, ranked by
+// rank_rays: a target whose lit rays carry more than GROUP_MEAN_MAX emitting
+// points on average is swept by lane pairs (sweep_ray_group); otherwise its
+// rays with more than GROUP_MAX points by lane pairs and the others a lane per
+// point (sweep_groups).  The choice depends only on the bins.  `scratch` holds
+// sweep_scratch_bytes(npix) bytes of shared memory; all threads call.
 template <int MODE, int NT>
 __device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, double* bins_eps, double* bins_e,
-                                             const Scales& sc) {
-    const int nr = a.nr, tid = threadIdx.x;
+                                             const Scales& sc, unsigned char* scratch) {
+    const int nr = a.nr, tid = threadIdx.x, lane = tid & 31;
     double Fk = 0.0;
-    if (MODE != 2) {
-        // a pair of consecutive lanes per ray: GB300 charges an FP64 warp
-        // instruction in full however few lanes it has, so the FP64 work is
-        // packed onto consecutive lanes
-        const int gl = tid & 1, lane = tid & 31;
+    if constexpr (MODE != 2) {
+        const int gl = tid & 1;
         const unsigned gmask = 3u << (lane & ~1);
         for (int k = tid >> 1; k < a.npix; k += NT / 2) {
             const double f = sweep_ray<MODE>(a, bins_a + k * nr, bins_eps + k * nr, a.use_e ? bins_e + k * nr : nullptr,
                                              sc, gl, gmask);
             if (gl == 0) Fk += f;
         }
+        return Fk;
     } else {
-        const int gl = tid % SG, lane = tid & 31;
-        const unsigned gmask = ((1u << SG) - 1u) << (lane & ~(SG - 1));
-        for (int k = tid / SG; k < a.npix; k += NT / SG) {
+    rank_rays<NT>(a, bins_eps, scratch);
+    const uint16_t* order = reinterpret_cast<const uint16_t*>(scratch);
+    const int* hdr = reinterpret_cast<const int*>(scratch + sweep_hdr_offset(a.npix));
+    const int gl = tid % SG;
+    const unsigned gmask = ((1u << SG) - 1u) << (lane & ~(SG - 1));
+    if (hdr[3] > GROUP_MEAN_MAX * hdr[0]) {                   // many points per ray: all by lane pairs
+        for (int r = tid / SG; r < hdr[0]; r += NT / SG) {
+            const int k = order[r];
             const double f = sweep_ray_group(a, bins_a + k * nr, bins_eps + k * nr,
                                              a.use_e ? bins_e + k * nr : nullptr, sc, gl, gmask);
             if (gl == 0) Fk += f;
         }
+        return Fk;
     }
-    return Fk;
+    // the pair-swept rays round-robin over the warps, so that no warp holds
+    // the CTA's barrier with all of them
+    constexpr int NW = NT / 32;
+    const int nbig = hdr[2];
+    for (int r = (tid >> 5) + NW * (lane / SG); r < nbig; r += NT / SG) {
+        const int k = order[r];
+        const double f = sweep_ray_group(a, bins_a + k * nr, bins_eps + k * nr,
+                                         a.use_e ? bins_e + k * nr : nullptr, sc, gl, gmask);
+        if (gl == 0) Fk += f;
+    }
+    return Fk + sweep_groups<NT>(a, bins_a, bins_eps, a.use_e ? bins_e : nullptr, sc, scratch);
+    }
 }
 
 template <int NT>
@@ -1009,6 +1189,7 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
     __shared__ int s_nacc;
     __shared__ __align__(16) WalkArgs s_a;                       // the current job
     __shared__ RadialSpread<MODE> s_node[NT];                    // the step's nodes to spread
+    static_assert(sizeof(RadialSpread<MODE>) * NT >= sweep_scratch_bytes(MAX_NPIX), "sweep scratch in s_node");
     __shared__ int s_pair0[NT + 1];                              // their first (node, ray) pair
     // W_p values kept by the setup threads: the FP64 form saves recomputing
     // them in FP64; in the FP32 form recomputing is cheaper than the shared
@@ -1404,7 +1585,8 @@ __device__ __forceinline__ void walk_body(const WalkArgs* __restrict__ jobs, con
             }
             continue;
         }
-        const double Fk = sweep_rays<MODE, NT>(a, bins_a, bins_eps, bins_e, sc);
+        const double Fk = sweep_rays<MODE, NT>(a, bins_a, bins_eps, bins_e, sc,
+                                                 reinterpret_cast<unsigned char*>(s_node));
         const double F = block_sum<NT>(Fk, s_red) + eps_self / (4.0 * PI_D * r_tp2);
         if (tid == 0) {
             const int64_t o = a.targets ? q : cell;
@@ -1420,6 +1602,22 @@ template <int MODE, int OUT, int NT, bool VAR>
 __global__ void __launch_bounds__(NT) k_walk(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
                                             int n_jobs, unsigned int* counter) {
     walk_body<MODE, OUT, NT, VAR>(jobs, job_end, n_jobs, counter);
+}
+
+// The double-FP32 form's walk with its CTAs per SM stated: five 128-thread
+// CTAs (its lane-group sweep would otherwise take enough registers to drop
+// it to four), or one wide CTA (left to the default, the compiler aims at two
+// and spills).
+template <int MODE, int OUT, int NT, bool VAR>
+__global__ void __launch_bounds__(NT, NT == 128 ? 5 : 1) k_walk5(const WalkArgs* __restrict__ jobs, const int64_t* __restrict__ job_end,
+                                                 int n_jobs, unsigned int* counter) {
+    walk_body<MODE, OUT, NT, VAR>(jobs, job_end, n_jobs, counter);
+}
+
+template <int MODE, int OUT, int NT, bool VAR>
+constexpr auto walk_kernel() {
+    if constexpr (MODE == 2 && !VAR) return &k_walk5<MODE, OUT, NT, VAR>;
+    else return &k_walk<MODE, OUT, NT, VAR>;
 }
 
 // The same walk with registers capped so that six 128-thread CTAs fit an SM:
@@ -1452,7 +1650,8 @@ __global__ void __launch_bounds__(NT) k_sweep_stored(WalkArgs a, const double* b
         }
         __syncthreads();
         const double Fk = sweep_rays<MODE, NT>(a, bins_a, bins_eps, bins_e,
-                                               Scales{a.scales_in[0], a.scales_in[1], a.scales_in[2]});
+                                               Scales{a.scales_in[0], a.scales_in[1], a.scales_in[2]},
+                                               smem + (size_t)(a.use_e ? 3 : 2) * nbins * sizeof(double));
         const double F = block_sum<NT>(Fk, s_red) + eps_self[q] / (4.0 * PI_D * 0.25);
         if (tid == 0) {
             if (a.F) a.F[q] = F * a.Fconv;
@@ -1550,7 +1749,7 @@ tr_status launch_persistent(K kernel, size_t smem, const WalkArgs* jobs, const i
 template <int MODE>
 bool wide_ctas_m(size_t smem) {
     int per_sm = 0;
-    const void* k = (const void*)k_walk<MODE, OUT_FUSED, WALK_NT, false>;
+    const void* k = (const void*)walk_kernel<MODE, OUT_FUSED, WALK_NT, false>();
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WALK_NT, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -1586,17 +1785,17 @@ tr_status launch_mode(int out, bool wide, size_t smem, const WalkArgs* jobs, con
     constexpr int F = OUT_FUSED;
     if constexpr (MODE != 2) {
         constexpr int D = OUT_DUMP, C = OUT_CD;
-        if (out == C) return launch_persistent<T>(k_walk<MODE, C, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+        if (out == C) return launch_persistent<T>(walk_kernel<MODE, C, T, VAR>(), smem, jobs, job_end, n_jobs, total, counter, st);
         if (out == D)
-            return wide ? launch_persistent<W>(k_walk<MODE, D, W, VAR>, smem, jobs, job_end, n_jobs, total, counter, st)
-                        : launch_persistent<T>(k_walk<MODE, D, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+            return wide ? launch_persistent<W>(walk_kernel<MODE, D, W, VAR>(), smem, jobs, job_end, n_jobs, total, counter, st)
+                        : launch_persistent<T>(walk_kernel<MODE, D, T, VAR>(), smem, jobs, job_end, n_jobs, total, counter, st);
     }
-    if (wide) return launch_persistent<W>(k_walk<MODE, F, W, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    if (wide) return launch_persistent<W>(walk_kernel<MODE, F, W, VAR>(), smem, jobs, job_end, n_jobs, total, counter, st);
     if constexpr (MODE != 0) {
-        if (more_ctas_capped((const void*)k_walk<MODE, F, T, VAR>, (const void*)k_walk_cap6<MODE, F, T, VAR>, smem))
+        if (more_ctas_capped((const void*)walk_kernel<MODE, F, T, VAR>(), (const void*)k_walk_cap6<MODE, F, T, VAR>, smem))
             return launch_persistent<T>(k_walk_cap6<MODE, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
     }
-    return launch_persistent<T>(k_walk<MODE, F, T, VAR>, smem, jobs, job_end, n_jobs, total, counter, st);
+    return launch_persistent<T>(walk_kernel<MODE, F, T, VAR>(), smem, jobs, job_end, n_jobs, total, counter, st);
 }
 
 template <bool VAR>
@@ -1715,7 +1914,7 @@ tr_status sweep_run(const tr_rays* r, double* F, double* e, uint8_t* ion, cudaSt
     a.Econv = r->Eu;
     a.F = F; a.E = e; a.ion = ion;
     a.scales_in = r->scales;
-    const size_t smem = (size_t)(r->use_e ? 3 : 2) * r->npix * r->nr * 8;
+    const size_t smem = (size_t)(r->use_e ? 3 : 2) * r->npix * r->nr * 8 + sweep_scratch_bytes(r->npix);
     auto kern = r->mode == 0 ? k_sweep_stored<0, WALK_NT>
                              : (r->mode == 1 ? k_sweep_stored<1, WALK_NT> : k_sweep_stored<2, WALK_NT>);
     tr_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
