@@ -902,7 +902,7 @@ __device__ double sweep_ray_group(const WalkArgs& a, const double* ba, double* b
 // the emitting points of all rays.
 constexpr int MAX_NPIX = 12 * 8 * 8;                  // N_side <= 8
 constexpr int GROUP_MAX = 32;                         // rays with more points go to lane pairs
-constexpr int GROUP_MEAN_MAX = 8;                     // lane groups while a lit ray has at most this many points on average
+constexpr int GROUP_MEAN_MAX = 14;                    // lane groups while a lit ray has at most this many points on average
 __host__ __device__ constexpr size_t sweep_hdr_offset(int npix) { return ((size_t)npix * 5 + 3) & ~(size_t)3; }
 __host__ __device__ constexpr size_t sweep_scratch_bytes(int npix) { return sweep_hdr_offset(npix) + 16; }
 
