@@ -17,6 +17,9 @@ AMR cluster, the 256^3 source-count series) are timed once each under
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 python bench.py --walk-only --workload W --precision P --reps R   (profiling:
     build once, then R launches of the fused walk kernel, nothing else)
+python bench.py --sweep-only --workload W --precision P --targets T --reps R
+    (profiling: walk and map T sampled cells once into stored ray bins,
+    then R launches of the stored-bins sweep)
 Under torchrun every rank solves its own copy of the workload (independent
 problems, weak scaling); rank 0 prints one JSON line.
 """
@@ -65,7 +68,10 @@ def parse():
     ap.add_argument("--configs", default="all", help="'all', 'none' or a comma list of extra workloads to time")
     ap.add_argument("--walk-only", action="store_true", help="profiling: R launches of the fused walk only")
     ap.add_argument("--precision", type=int, default=1, help="--walk-only: tr_precision of the tree")
-    ap.add_argument("--reps", type=int, default=2, help="--walk-only: walk launches")
+    ap.add_argument("--reps", type=int, default=2, help="--walk-only / --sweep-only: launches")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="profiling: R launches of the stored-bins sweep over a sample of targets")
+    ap.add_argument("--targets", type=int, default=65536, help="--sweep-only: sampled targets")
     return ap.parse_args()
 
 
@@ -252,6 +258,34 @@ def run_walk_only(args):
                       "counters": B.tr_tree_stats(tree), "tree": tree.info(), "ms_per_launch": ms}), flush=True)
 
 
+def run_sweep_only(args):
+    """Profiling entry for the sweep alone: walk and map a seeded sample of
+    `targets` cells once into stored ray bins (tr_walk_map), then `reps`
+    launches of the stored-bins sweep (tr_ray_sweep, CUDA events around
+    each)."""
+    import torch
+    import paper_2105_09644_gb300 as pkg
+    pkg.build()
+    from paper_2105_09644_gb300 import binding as B
+    devn = torch.device("cuda", 0)
+    pr = make_problem(B, args.workload, devn)
+    tree = pr["build"](pr["grid"], pr["src"], pr["params"](args.precision))
+    g = torch.Generator().manual_seed(5)
+    tg = torch.randint(0, pr["ncell"], (args.targets,), generator=g, dtype=torch.int64).to(devn)
+    rays = B.tr_walk_map(tree, targets=tg)
+    F = torch.empty(args.targets, dtype=torch.float64, device=devn)
+    ms = []
+    for _ in range(args.reps):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        B.tr_ray_sweep(rays, F)
+        s1.record()
+        torch.cuda.synchronize()
+        ms.append(s0.elapsed_time(s1))
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "form": FORM_NAMES[args.precision],
+                      "targets": args.targets, "tree": tree.info(), "sweep_ms_per_launch": ms}), flush=True)
+
+
 def l2_copy_peak(devn, mb=32, reps=20):
     """L2 bandwidth ceiling: device copies between two `mb` MB buffers that
     stay resident in the 129 MB L2 (read + write bytes), `reps` of them
@@ -299,6 +333,9 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    if args.sweep_only:
+        run_sweep_only(args)
+        return
     if args.walk_only:
         run_walk_only(args)
         return

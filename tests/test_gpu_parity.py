@@ -8,6 +8,7 @@ FP32 forms) away from the ionisation front, with the ionised/neutral
 classification identical except within one cell of the front.  No fraction
 of the cells is exempt from these bars, at any size.
 """
+import json
 import math
 
 import numpy as np
@@ -103,6 +104,13 @@ def compare_fields(F, ion, F_orc, ion_orc, N, rtol, kappa=0.0, free_fn=None):
     # cells that differ in class lie within one cell of the oracle's front
     diff = ion != ion_orc
     assert not np.any(diff & inner)
+    stats = {"cells": int(ion.size), "interior_lit": int(lit.size),
+             "rel_err_max": float(err.max()) if lit.size else 0.0,
+             "rel_err_p99": float(np.percentile(err, 99)) if lit.size else 0.0,
+             "rel_err_median": float(np.median(err)) if lit.size else 0.0,
+             "class_flips_at_front": int(diff.sum()), "front_cells": int((~inner).sum())}
+    print("field errors vs oracle:", json.dumps(stats))
+    return stats
 
 
 # --------------------------------------------------------------------------
