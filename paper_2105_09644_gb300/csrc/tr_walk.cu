@@ -1094,9 +1094,11 @@ __device__ __forceinline__ double sweep_rays(const WalkArgs& a, double* bins_a, 
     const int* hdr = reinterpret_cast<const int*>(scratch + sweep_hdr_offset(a.npix));
     const int gl = tid % SG;
     const unsigned gmask = ((1u << SG) - 1u) << (lane & ~(SG - 1));
-    if (hdr[3] > GROUP_MEAN_MAX * hdr[0]) {                   // many points per ray: all by lane pairs
-        for (int r = tid / SG; r < hdr[0]; r += NT / SG) {
-            const int k = order[r];
+    if (hdr[3] > GROUP_MEAN_MAX * hdr[0]) {
+        // many points per ray: every ray by lane pairs, in ray order (ranked
+        // order would put the heaviest rays in one warp, which then holds
+        // the CTA's barrier)
+        for (int k = tid / SG; k < a.npix; k += NT / SG) {
             const double f = sweep_ray_group(a, bins_a + k * nr, bins_eps + k * nr,
                                              a.use_e ? bins_e + k * nr : nullptr, sc, gl, gmask);
             if (gl == 0) Fk += f;
